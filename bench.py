@@ -1,0 +1,350 @@
+"""Throughput of the fused wetting-LB step on GB300, in MLUPS and as a fraction
+of the HBM roofline.
+
+Workload: the 8192x4096 D2Q9 lattice with 64 drops (R ~ U[40, 120], seed 1) on a
+heterogeneous wall (thickness 3 + 1.5 sin(2 pi 8 x / nx)), exponential
+pseudo-potential G = -5.5, tau = 1, core 0.1 / tail 0.05 wall potential.
+A bench "step" is one LB time step over the whole lattice: one launch of the
+fused kernel.  Population buffers (2 x 1.2 GB in FP32) are far larger than L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16s|bf16s|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+N > 1 (under torch.distributed.run): independent replicas, one per GPU, no
+collective on the data path ("scaling": "weak"); value = all ranks' lattice
+updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NY = 8192, 4096
+WORKLOAD = ("8192x4096 D2Q9 pseudo-potential wetting LB, 64 drops R~U[40,120] seed 1 on a "
+            "heterogeneous wall (T(x)=3+1.5 sin(2 pi 8x/nx)), exp psi G=-5.5, tau=1, "
+            "core 0.1 / tail 0.05")
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16", "bf16s": "bf16"}
+BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
+KERNEL_SOURCES = ["step_kernel.cuh", "node.cuh", "tma.cuh", "lattice.cuh", "launch.cuh",
+                  "step_impl.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1202_6130_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(storage: str):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"step_{storage}_d2q9_8192x4096.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_hash:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_identifier(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def dist_max(world: int, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(rows: int, steps: int):
+    """Runs the FP64 oracle on rows [0, rows) of the workload (a periodic band of
+    the full width, wall included); returns (node updates, seconds)."""
+    import numpy as np
+    import workloads as W
+    from oracle import lbm_oracle as O
+    w = W.large_multi_droplet(with_fields=False)
+    T = 3.0 + 1.5 * np.sin(2.0 * np.pi * 8.0 * np.arange(NX) / NX)
+    rho = W.droplet_density(NX, rows, w.meta["centers"], w.meta["radii"], 2.0, 0.15, 2.0)
+    phi, pr, pa = W.wall_core_tail(W.wall_distance_slab(NX, rows), T[None, :])
+    p = O.Params(lattice=O.D2Q9, tau=1.0, G=-5.5)
+    wall = O.Wall(phi, pr, pa, 0.1, 0.05, 1.0)
+    z = np.zeros_like(rho)
+    f = O.initial_populations(p, rho, z, z)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.step(p, wall, f)
+    dt = time.perf_counter() - t0
+    return NX * rows * steps, dt
+
+
+def cpu_baseline(target_s: float = 15.0):
+    rows = 256
+    n, dt = oracle_sample(rows, 1)
+    steps = max(1, int(target_s / max(dt, 1e-3)))
+    n, dt = oracle_sample(rows, steps)
+    return {"value": n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, rows 0..{rows - 1} of the 8192-wide workload as a "
+                      f"periodic {NX}x{rows} band with its wall, {steps} steps, one thread"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    budget = 150.0
+    total = args.steps + args.warmup
+    # calibrate: seconds per node-step of the oracle on this host
+    n, dt = oracle_sample(16, 1)
+    per = dt / n
+    rows = int(max(4, min(512, budget / total / per / NX)))
+    for _ in range(args.warmup):
+        oracle_sample(rows, 1)
+    n, dt = 0, 0.0
+    for _ in range(args.steps):
+        a, b = oracle_sample(rows, 1)
+        n += a
+        dt += b
+    v = n / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+                                        "sample_rows": rows},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one oracle step on a periodic {NX}x{rows} band "
+                                   "(rows 0.. of the workload, wall included)"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1202_6130_gb300 as pkg
+    import workloads as W
+    pkg.load()
+
+    nx, ny = (int(v) for v in args.size.lower().split("x"))
+    w = W.large_multi_droplet(nx=nx, ny=ny, noise_amp=0.0)
+    sim = pkg.Simulation.from_workload(w, storage=args.storage)
+    lay = sim.layout()
+    stream = torch.cuda.current_stream()
+    N = nx * ny
+
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region: K launches of the fused step --------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_identifier(torch, local)) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    t = dist_max(world, t_local)
+    mlups = world * N * args.steps / t / 1e6
+    sim.sync()
+
+    # ---- end to end through the public API with pinned host buffers --------
+    lbm_per_e2e = 1000
+    n_e2e = max(1, args.steps // lbm_per_e2e)
+    rho_h = torch.from_numpy(w.rho).pin_memory().numpy()
+    z = torch.zeros((ny, nx), dtype=torch.float64).pin_memory().numpy()
+    outs = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    sim.set_equilibrium(rho_h, z, z)
+    sim.step(10)
+    sim.moments(outs)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sim.set_equilibrium(rho_h, z, z)
+        sim.step(lbm_per_e2e)
+        sim.moments(outs)
+    t_e2e = dist_max(world, time.perf_counter() - t0)
+    e2e = world * N * lbm_per_e2e * n_e2e / t_e2e / 1e6
+    assert np.isfinite(outs[0]).all()
+
+    # ---- roofline of the fused kernel ----------------------------------------
+    peak, peak_kind = measured_peaks()
+    b_node = 2 * 9 * BYTES[args.storage]
+    achieved = b_node * N * args.steps / t_local / 1e9
+    traffic = ncu_traffic(args.storage)
+    clocks = clk.summary()
+    sim.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.storage], "data": "synthetic",
+        "config": {"workload": WORKLOAD if (nx, ny) == (NX, NY) else
+                   WORKLOAD.replace("8192x4096", f"{nx}x{ny}"), "nx": nx, "ny": ny,
+                   "lattice": "D2Q9",
+                   "storage": args.storage, "parallelism": f"replicas{world}",
+                   "l2": "no flush: the 2 population buffers (2x%.2f GB) exceed L2" %
+                         (9 * BYTES[args.storage] * N / 1e9),
+                   "launch": {k: lay[k] for k in ("strip_width", "tile_rows", "grid_x",
+                                                   "grid_y", "stages")}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_node": b_node,
+                     "kernel": "lbm::step_kernel"},
+        "e2e": {"value": e2e, "unit": "MLUPS",
+                "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
+                "lbm_steps_per_e2e_step": lbm_per_e2e, "e2e_steps": n_e2e,
+                "path": "Simulation.set_equilibrium(pinned rho,u) -> step -> moments(pinned)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=list(DTYPE))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=f"{NX}x{NY}",
+                    help="lattice size NXxNY (the same recipe at another size, for profiling)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

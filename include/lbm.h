@@ -1,0 +1,207 @@
+/*
+ * lbm.h -- C ABI of the GB300 pseudo-potential wetting lattice-Boltzmann engine.
+ *
+ * The engine advances the mesoscopic wetting model of Colosqui, Kavousanakis,
+ * Papathanasiou & Kevrekidis (arXiv:1202.6130), Sec. II: per time step and per
+ * lattice node it pulls the populations (streaming), forms rho and j
+ * (Eqs. M0, M1), the pseudo-potential psi (Eq. EOS or the exponential form),
+ * the fluid-fluid force (Eq. force_SC), the long-range fluid-solid force and
+ * the short-range wall momentum exchange weighted by the wall probability
+ * (Eqs. force_SC_FS, pseudopotential, wall_shift), then relaxes with BGK plus
+ * the exact-difference-method forcing (Eq. BE-BGK, Sec. II B).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (LBM_OK or a negative LBM_E* code) and
+ *     never throws across the ABI.  After LBM_ECUDA the context is poisoned:
+ *     later calls except lbm_destroy / lbm_last_error return LBM_ESTATE.
+ *   - Host arrays are row-major [y][x] (x fastest, y = 0 at the bottom) in
+ *     FP64; population arrays are [i][y][x] with i in the lattice table order
+ *     (D2Q9: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1);
+ *     D2Q21: Table I order, states 1-4 axes speed 1, 5-8 diagonals, 9-12 axes
+ *     speed 2, 13-16 (+-2,+-2), 17-20 axes speed 3, 21 rest; counter-clockwise
+ *     from +x inside each group).
+ *   - The caller owns every host buffer; the engine copies what it needs
+ *     during the call and keeps no pointer to it.  The context owns all device
+ *     memory, obtained from the caller's lbm_allocator if one is given, else
+ *     from cudaMalloc.
+ *   - The lattice is fully periodic in x and y.  The solid exists only through
+ *     the wall fields of lbm_set_wall (a wall "at y = 0" is a slab across the
+ *     periodic seam).
+ *   - A population f_i(x, t) given to or returned by the engine is the value
+ *     just after streaming, before collision, at time t.
+ *   - Work is enqueued on the context's CUDA stream.  lbm_step returns after
+ *     enqueueing (unless a periodic check is due); calls that fill host
+ *     buffers synchronise the stream.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Device-memory provider.  alloc returns a device pointer aligned to at least
+ * 256 bytes, or NULL on failure (the engine then returns LBM_ENOMEM); free
+ * releases it.  Both may be called from any engine entry point. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} lbm_allocator;
+
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,     /* bad argument: null pointer, size, tau <= 0.5, ... */
+  LBM_ENOMEM = -2,     /* the allocator returned NULL */
+  LBM_ECUDA = -3,      /* a CUDA call failed; the context is poisoned */
+  LBM_ESTATE = -4,     /* call not valid in this state (poisoned, no populations) */
+  LBM_ENONFINITE = -5, /* a periodic check found a non-finite density */
+  LBM_ETIMEOUT = -6    /* a bounded device-side wait gave up */
+};
+
+enum { LBM_D2Q9 = 9, LBM_D2Q21 = 21 };
+
+/* Population storage.  FP16S / BF16S store the deviation f_i - w_i * shift_rho
+ * rounded to nearest-even in 16 bits; all arithmetic is FP32. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 };
+
+/* Pseudo-potential psi(rho):
+ *   LBM_PSI_EXP: rho0 * (1 - exp(-rho / rho0))          (Shan-Chen form)
+ *   LBM_PSI_EOS: sqrt(2 (rho theta - p_EOS(rho)))       (Sec. II, Eq. EOS)  */
+enum { LBM_PSI_EXP = 0, LBM_PSI_EOS = 1 };
+
+/* The problem statement of Sec. II: lattice, relaxation time tau (Eq. BE-BGK),
+ * fluid-fluid coupling, equation of state, body force.  The fluid-fluid force
+ * is F_FF = -G psi(x) sum_i w_i psi(x + r_i) r_i (Eq. force_SC); the paper's
+ * EOS fluid corresponds to G = -1/theta. */
+typedef struct {
+  int32_t nx, ny;        /* lattice size, >= 1 each */
+  int32_t lattice;       /* LBM_D2Q9 or LBM_D2Q21 */
+  int32_t storage;       /* LBM_FP64 .. LBM_BF16S */
+  int32_t psi_kind;      /* LBM_PSI_EXP or LBM_PSI_EOS */
+  int32_t project;       /* 1: projection step (Sec. II, after Eq. f2) before collision */
+  double tau;            /* > 0.5 */
+  double G;              /* fluid-fluid coupling */
+  double rho0;           /* LBM_PSI_EXP scale, > 0 */
+  double eos_theta_v;    /* Eq. EOS slopes (absolute, not divided by theta) */
+  double eos_theta_u;
+  double eos_theta_l;
+  double eos_rho1;       /* Eq. EOS knots rho_1 < rho_2 */
+  double eos_rho2;
+  double body_force[2];  /* uniform force density added on every node */
+  double shift_rho;      /* FP16S/BF16S shift; <= 0: mean initial density */
+  int32_t check_every;   /* lbm_step checks for non-finite rho every K steps; 0 = never */
+  int32_t tile_rows;     /* rows per CTA strip segment; 0 = chosen by the engine */
+} lbm_params;
+
+/* Fills *p with defaults: D2Q9, FP32, exponential psi, tau 1, G -5.5, rho0 1,
+ * the paper's EOS parameters scaled by theta = 1/3, no body force. */
+int lbm_params_default(lbm_params* p);
+
+/* Creates a context.  a may be NULL (cudaMalloc is used); stream may be NULL
+ * (the legacy default stream).  The population state is undefined until
+ * lbm_set_populations or lbm_set_equilibrium succeeds.  *out is NULL on error. */
+int lbm_create(const lbm_params* p, const lbm_allocator* a, void* cuda_stream, lbm_ctx** out);
+
+/* Replaces the CUDA stream on which later calls enqueue work. */
+int lbm_set_stream(lbm_ctx* c, void* cuda_stream);
+
+/* Static wall fields (Sec. II "Fluid-Solid interactions", Eqs. force_SC_FS,
+ * pseudopotential, wall_shift).  phi_s: wall probability phi_S; psi_r, psi_a:
+ * the repulsive and attractive potentials psi_R-bar, psi_A-bar; each [ny][nx],
+ * NULL meaning identically 0.  The fluid-solid pseudo-potential is
+ * psi_FS = G_A psi_A-bar - G_R psi_R-bar (G_R, G_A >= 0 are strengths: the core
+ * repels, the tail attracts).  epsilon >= 1 is the exponent of phi_S^epsilon.
+ * u_wall: [2][ny][nx] wall velocity (x plane then y plane) or NULL (solid at rest).
+ * The engine precomputes phi_S^epsilon and S(x) = sum_i w_i psi_FS(x + r_i) r_i
+ * on the device; the long-range force is then rho(x) S(x). */
+int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const double* psi_a,
+                 double G_R, double G_A, double epsilon, const double* u_wall);
+
+/* Sets the populations f_i(x, t) from a host array [Q][ny][nx]. */
+int lbm_set_populations(lbm_ctx* c, const double* f);
+
+/* Sets f_i = f_i^eq(rho, u) (Eq. feqc, second-order Hermite form) plus an
+ * optional perturbation dfi [Q][ny][nx] (NULL = none).  rho, ux, uy: [ny][nx]. */
+int lbm_set_equilibrium(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                        const double* dfi);
+
+/* Advances nsteps >= 0 time steps (one fused kernel launch per step).  Returns
+ * after enqueueing, or LBM_ENONFINITE when check_every > 0 and a check found a
+ * non-finite density (the state is then kept as it was after that step). */
+int lbm_step(lbm_ctx* c, int64_t nsteps);
+
+/* Reads rho and the reported velocity u = (j + F/2) / rho of the current state
+ * into host arrays [ny][nx] (any may be NULL).  Synchronises the stream. */
+int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy);
+
+/* As lbm_moments, but into DEVICE arrays of ny*nx doubles, enqueued on the
+ * stream without synchronising. */
+int lbm_moments_device(lbm_ctx* c, double* d_rho, double* d_ux, double* d_uy);
+
+/* Reads the populations f_i(x, t) into a host array [Q][ny][nx].  Synchronises. */
+int lbm_get_populations(lbm_ctx* c, double* f);
+
+/* out[0] = sum rho, out[1..2] = sum (j + F/2) over the lattice, FP64 with
+ * compensated (Neumaier) summation per thread.  Synchronises. */
+int lbm_totals(lbm_ctx* c, double out[3]);
+
+/* Steps taken since the populations were last set. */
+int lbm_steps_done(const lbm_ctx* c, int64_t* out);
+
+/* Waits for all work enqueued by this context. */
+int lbm_sync(lbm_ctx* c);
+
+/* Frees the context and its device memory; NULL is accepted.  Always LBM_OK. */
+int lbm_destroy(lbm_ctx* c);
+
+/* Human-readable description of the last error on c ("" if none), owned by c.
+ * lbm_last_error(NULL) reports errors of calls that had no context yet. */
+const char* lbm_last_error(const lbm_ctx* c);
+
+/* Layout facts for measurement: bytes per node per step that the population
+ * traffic needs (2 Q s), the padded row pitch in elements, and the launch shape
+ * (strip width, rows per CTA, grid) of the fused step. */
+typedef struct {
+  int64_t bytes_per_node;
+  int64_t pitch;
+  int32_t strip_width;
+  int32_t tile_rows;
+  int32_t grid_x, grid_y;
+  int32_t stages;
+  int32_t ghost_x, ghost_y;
+  int64_t device_bytes;
+} lbm_layout;
+int lbm_get_layout(const lbm_ctx* c, lbm_layout* out);
+
+/* ---- wall-function helpers (initialisation; FP64) ------------------------ */
+
+/* Recursive Gaussian filter of the Appendix (Eq. iteration): G^(0) = 1 on the
+ * solid nodes (solid[y*nx+x] != 0) and 0 elsewhere; each pass sets
+ * G^(n)(x) = sum_i w_i G^(n-1)(x + r_i) on the periodic lattice and resets G to 1
+ * on the solid nodes.  Outputs phi_S = G^(n_att), psi_R-bar = G^(n_rep),
+ * psi_A-bar = G^(n_att) - G^(n_rep), each [ny][nx] host (any may be NULL).
+ * Runs on the current CUDA device; 0 <= n_rep <= n_att. */
+int lbm_wall_gaussian_filter(int32_t nx, int32_t ny, int32_t lattice, const uint8_t* solid,
+                             int32_t n_rep, int32_t n_att, double* phi_s, double* psi_r,
+                             double* psi_a);
+
+/* Closed-form wall fields from a distance-to-solid map dist [ny][nx] and a
+ * thickness per column (thickness[x], nx entries): phi_S = (1 - tanh((d - T/2)
+ * / (T/4))) / 2, zeroed below phi_cut; psi_R-bar = exp(-d / lambda) -
+ * exp(-core_cut / lambda) for d < core_cut, else 0; psi_A-bar = (1 + d)^-p -
+ * (1 + tail_cut)^-p for d < tail_cut, else 0.  Host-only. */
+int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double* thickness,
+                       double core_lambda, double core_cut, double tail_exp, double tail_cut,
+                       double phi_cut, double* phi_s, double* psi_r, double* psi_a);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

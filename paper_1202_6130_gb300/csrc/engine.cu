@@ -1,0 +1,731 @@
+// C ABI of the engine (include/lbm.h): context life cycle, device memory,
+// TMA descriptors, launch-shape selection and dispatch over (lattice, storage).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launch.cuh"
+
+using namespace lbm;
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct lbm_ctx {
+  lbm_params p{};
+  int Q = 9, R = 1, GX = 0, GY = 0, esize = 4, W = 128, NS = 8;
+  int64_t pitch = 0, rows = 0, plane = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding the current state
+  CUtensorMap tmap[2];
+  // wall (compute precision: double for FP64 storage, float otherwise)
+  void* wall_phie = nullptr;
+  void* wall_sx = nullptr;
+  void* wall_sy = nullptr;
+  void* wall_uwx = nullptr;
+  void* wall_uwy = nullptr;
+  uint8_t* wall_flags = nullptr;
+  int nchunk = 0;
+  bool has_wall = false;
+  uint32_t* d_status = nullptr;
+  double* d_partials = nullptr;
+  int nparts = 0;
+  double* d_out3 = nullptr;
+  cudaStream_t stream = nullptr;
+  lbm_allocator alloc{};
+  bool user_alloc = false;
+  std::vector<void*> owned;
+  std::string err;
+  bool poisoned = false;
+  bool has_state = false;
+  int64_t steps = 0;
+  double rho_s = 0.0;
+  int tile_rows = 0, grid_x = 0, grid_y = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;  // errors of calls without a context
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = msg;
+    if (code == LBM_ECUDA) c->poisoned = true;
+  } else {
+    g_err = msg;
+  }
+  return code;
+}
+
+#define CK(ctx, ...)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (__VA_ARGS__);                                                     \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((ctx), LBM_ECUDA, "%s failed: %s (%s:%d)", #__VA_ARGS__,                \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+  } while (0)
+
+void* dalloc(lbm_ctx* c, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->user_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->owned.push_back(p);
+  return p;
+}
+
+void dfree(lbm_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->owned.begin(), c->owned.end(), p);
+  if (it != c->owned.end()) c->owned.erase(it);
+  if (c->user_alloc)
+    c->alloc.free(p, c->alloc.user);
+  else
+    cudaFree(p);
+}
+
+// Scoped temporary device allocation.
+struct Tmp {
+  lbm_ctx* c;
+  void* p;
+  Tmp(lbm_ctx* c_, size_t bytes) : c(c_), p(bytes ? dalloc(c_, bytes) : nullptr) {}
+  ~Tmp() {
+    if (p) {
+      cudaStreamSynchronize(c->stream);
+      dfree(c, p);
+    }
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+int guard(lbm_ctx* c) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "null context");
+  if (c->poisoned) return fail(c, LBM_ESTATE, "context poisoned by an earlier CUDA error: %s", c->err.c_str());
+  return LBM_OK;
+}
+
+// --- dispatch over (lattice, storage) ---------------------------------------
+template <typename F> int dispatch(int Q, int storage, F&& fn) {
+  switch (Q * 10 + storage) {
+    case 90: return fn.template operator()<9, double>();
+    case 91: return fn.template operator()<9, float>();
+    case 92: return fn.template operator()<9, __half>();
+    case 93: return fn.template operator()<9, __nv_bfloat16>();
+    case 210: return fn.template operator()<21, double>();
+    case 211: return fn.template operator()<21, float>();
+    case 212: return fn.template operator()<21, __half>();
+    case 213: return fn.template operator()<21, __nv_bfloat16>();
+  }
+  return LBM_EINVAL;
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeFn>(p);
+  }();
+  return fn;
+}
+
+template <typename S> CUtensorMapDataType tma_type();
+template <> CUtensorMapDataType tma_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <> CUtensorMapDataType tma_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> CUtensorMapDataType tma_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <> CUtensorMapDataType tma_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+
+template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
+  using Sh = ConfigShape<Q, S>;
+  EncodeFn enc = get_encode();
+  if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  cuuint64_t dims[3] = {(cuuint64_t)(c->p.nx + 2 * Sh::GX), (cuuint64_t)c->rows, (cuuint64_t)Q};
+  cuuint64_t strides[2] = {(cuuint64_t)(c->pitch * sizeof(S)),
+                           (cuuint64_t)(c->plane * sizeof(S))};
+  cuuint32_t box[3] = {(cuuint32_t)Sh::BW, 1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&c->tmap[which], tma_type<S>(), 3, c->buf[which], dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return LBM_OK;
+}
+
+// Rows per CTA: the grid (strips x segments) should fill whole waves of
+// resident CTAs while keeping the 2R halo rows per segment a small fraction.
+int choose_tile_rows(int nx, int ny, int W, int R, int ctas_per_sm, int num_sms) {
+  const int gx = (nx + W - 1) / W;
+  const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
+  double best = -1.0;
+  int best_L = ny;
+  for (int L = 1; L <= ny; ++L) {
+    const int gy = (ny + L - 1) / L;
+    if (L > 1 && (ny + L - 2) / (L - 1) == gy) continue;  // same grid as a smaller L
+    const int64_t ctas = (int64_t)gx * gy;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double fill = (double)ctas / (double)(waves * slots);
+    const double halo = (double)L / (double)(L + 2 * R);
+    // mild preference for fewer, longer segments (pipeline start-up per CTA)
+    const double startup = (double)L / (double)(L + 8);
+    const double score = fill * halo * startup;
+    if (score > best + 1e-12) {
+      best = score;
+      best_L = L;
+    }
+  }
+  return best_L;
+}
+
+template <int Q, typename S> int setup_layout(lbm_ctx* c) {
+  using Sh = ConfigShape<Q, S>;
+  c->Q = Q;
+  c->R = Sh::R;
+  c->GX = Sh::GX;
+  c->GY = Sh::GY;
+  c->esize = (int)sizeof(S);
+  c->W = StepConfig<Q, S>::W;
+  c->NS = StepConfig<Q, S>::NS;
+  c->pitch = ((int64_t)(c->p.nx + 2 * Sh::GX) + 31) / 32 * 32;
+  c->rows = c->p.ny + 2 * Sh::GY;
+  c->plane = c->pitch * c->rows;
+  const size_t bytes = (size_t)c->plane * Q * sizeof(S);
+  for (int b = 0; b < 2; ++b) {
+    c->buf[b] = dalloc(c, bytes);
+    if (!c->buf[b]) return fail(c, LBM_ENOMEM, "population buffer of %zu bytes", bytes);
+    CK(c, cudaMemsetAsync(c->buf[b], 0, bytes, c->stream));
+    int rc = make_tmap<Q, S>(c, b);
+    if (rc) return rc;
+  }
+  int dev = 0, sms = 0;
+  CK(c, cudaGetDevice(&dev));
+  CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int cps = step_ctas_per_sm<Q, S>();
+  if (cps <= 0) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, LBM_ECUDA, "step kernel cannot be resident (%s)", cudaGetErrorString(e));
+  }
+  c->tile_rows = c->p.tile_rows > 0 ? std::min(c->p.tile_rows, c->p.ny)
+                                    : choose_tile_rows(c->p.nx, c->p.ny, c->W, c->R, cps, sms);
+  c->grid_x = (c->p.nx + c->W - 1) / c->W;
+  c->grid_y = (c->p.ny + c->tile_rows - 1) / c->tile_rows;
+  return LBM_OK;
+}
+
+template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
+  const lbm_params& p = c->p;
+  Physics<T> P;
+  P.omega = (T)(1.0 / p.tau);
+  P.one_m_omega = (T)(1.0 - 1.0 / p.tau);
+  P.G = (T)p.G;
+  P.rho0 = (T)p.rho0;
+  P.eos_tv = (T)p.eos_theta_v;
+  P.eos_tu = (T)p.eos_theta_u;
+  P.eos_tl = (T)p.eos_theta_l;
+  P.eos_r1 = (T)p.eos_rho1;
+  P.eos_r2 = (T)p.eos_rho2;
+  const double p1 = p.eos_rho1 * p.eos_theta_v;
+  const double p2 = p.eos_rho1 * p.eos_theta_v + (p.eos_rho2 - p.eos_rho1) * p.eos_theta_u;
+  P.eos_p1 = (T)p1;
+  P.eos_p2 = (T)p2;
+  P.bfx = (T)p.body_force[0];
+  P.bfy = (T)p.body_force[1];
+  P.rho_s = (T)c->rho_s;
+  P.psi_kind = p.psi_kind;
+  P.project = p.project;
+  return P;
+}
+
+template <int Q, typename S>
+int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, int momentum,
+             S* fout) {
+  using T = typename Codec<S>::T;
+  StepArgs<T, S> a{};
+  a.phys = make_physics<T>(c);
+  a.wall.phie = static_cast<const T*>(c->wall_phie);
+  a.wall.sx = static_cast<const T*>(c->wall_sx);
+  a.wall.sy = static_cast<const T*>(c->wall_sy);
+  a.wall.uwx = static_cast<const T*>(c->wall_uwx);
+  a.wall.uwy = static_cast<const T*>(c->wall_uwy);
+  a.wall.flags = c->wall_flags;
+  a.wall.nchunk = c->nchunk;
+  a.wall.active = c->has_wall ? 1 : 0;
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.pitch = (int32_t)c->pitch;
+  a.tile_rows = c->tile_rows;
+  a.plane = c->plane;
+  a.fout = fout;
+  a.out_rho = o_rho;
+  a.out_ux = o_ux;
+  a.out_uy = o_uy;
+  a.momentum = momentum;
+  a.status = c->d_status;
+  CK(c, launch_step<Q, S>(c->tmap[c->cur], a, dim3(c->grid_x, c->grid_y), c->stream, mode));
+  return LBM_OK;
+}
+
+int check_params(const lbm_params* p) {
+  if (!p) return fail(nullptr, LBM_EINVAL, "null params");
+  if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "lattice size %dx%d", p->nx, p->ny);
+  if ((int64_t)p->nx * p->ny > (int64_t)1 << 31)
+    return fail(nullptr, LBM_EINVAL, "lattice of %lld nodes exceeds 2^31", (long long)p->nx * p->ny);
+  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D2Q21)
+    return fail(nullptr, LBM_EINVAL, "lattice %d", p->lattice);
+  if (p->storage < LBM_FP64 || p->storage > LBM_BF16S)
+    return fail(nullptr, LBM_EINVAL, "storage %d", p->storage);
+  if (p->psi_kind != LBM_PSI_EXP && p->psi_kind != LBM_PSI_EOS)
+    return fail(nullptr, LBM_EINVAL, "psi_kind %d", p->psi_kind);
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+    return fail(nullptr, LBM_EINVAL, "tau must be > 0.5 (got %g)", p->tau);
+  if (p->psi_kind == LBM_PSI_EXP && !(p->rho0 > 0.0))
+    return fail(nullptr, LBM_EINVAL, "rho0 must be > 0");
+  if (p->psi_kind == LBM_PSI_EOS && !(p->eos_rho1 < p->eos_rho2))
+    return fail(nullptr, LBM_EINVAL, "EOS knots must satisfy rho1 < rho2");
+  if (p->check_every < 0 || p->tile_rows < 0) return fail(nullptr, LBM_EINVAL, "negative count");
+  return LBM_OK;
+}
+
+// Shift for FP16S / BF16S: the configured value, else the mean of rho.
+int set_shift_from_rho(lbm_ctx* c, const double* d_rho) {
+  if (c->p.storage != LBM_FP16S && c->p.storage != LBM_BF16S) {
+    c->rho_s = 0.0;
+    return LBM_OK;
+  }
+  if (c->p.shift_rho > 0.0) {
+    c->rho_s = c->p.shift_rho;
+    return LBM_OK;
+  }
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  CK(c, launch_reduce3(d_rho, nullptr, nullptr, N, c->d_partials, c->nparts, c->d_out3, c->stream));
+  double h[3];
+  CK(c, cudaMemcpyAsync(h, c->d_out3, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->rho_s = h[0] / (double)N;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int lbm_params_default(lbm_params* p) {
+  if (!p) return fail(nullptr, LBM_EINVAL, "null params");
+  std::memset(p, 0, sizeof *p);
+  p->nx = 128;
+  p->ny = 64;
+  p->lattice = LBM_D2Q9;
+  p->storage = LBM_FP32;
+  p->psi_kind = LBM_PSI_EXP;
+  p->tau = 1.0;
+  p->G = -5.5;
+  p->rho0 = 1.0;
+  const double th = 1.0 / 3.0;
+  p->eos_theta_v = 0.25 * th;
+  p->eos_theta_u = -0.25 * th;
+  p->eos_theta_l = 1.0 * th;
+  p->eos_rho1 = 0.222;
+  p->eos_rho2 = 0.869;
+  return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, const lbm_allocator* a, void* cuda_stream, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "null output pointer");
+  *out = nullptr;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (a && (!a->alloc || !a->free)) return fail(nullptr, LBM_EINVAL, "allocator without alloc/free");
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation");
+  c->p = *p;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (a) {
+    c->alloc = *a;
+    c->user_alloc = true;
+  }
+  rc = dispatch(p->lattice, p->storage, [&]<int Q, typename S>() { return setup_layout<Q, S>(c); });
+  if (rc == LBM_OK) {
+    c->d_status = static_cast<uint32_t*>(dalloc(c, 256));
+    c->nparts = 1024;
+    c->d_partials = static_cast<double*>(dalloc(c, sizeof(double) * 6 * c->nparts));
+    c->d_out3 = static_cast<double*>(dalloc(c, 256));
+    if (!c->d_status || !c->d_partials || !c->d_out3)
+      rc = fail(c, LBM_ENOMEM, "status / reduction buffers");
+    else if (cudaMemsetAsync(c->d_status, 0, 256, c->stream) != cudaSuccess)
+      rc = fail(c, LBM_ECUDA, "cudaMemsetAsync status");
+  }
+  if (rc != LBM_OK) {
+    g_err = c->err;
+    lbm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
+  int rc = guard(c);
+  if (rc) return rc;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LBM_OK;
+}
+
+int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const double* psi_a,
+                 double G_R, double G_A, double epsilon, const double* u_wall) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!(epsilon > 0.0) || !std::isfinite(G_R) || !std::isfinite(G_A))
+    return fail(c, LBM_EINVAL, "wall parameters (epsilon %g, G_R %g, G_A %g)", epsilon, G_R, G_A);
+  const int nx = c->p.nx, ny = c->p.ny;
+  const int64_t N = (int64_t)nx * ny;
+  const size_t tsz = c->p.storage == LBM_FP64 ? sizeof(double) : sizeof(float);
+  if (!c->wall_phie) {
+    c->nchunk = (nx + 31) / 32;
+    c->wall_phie = dalloc(c, N * tsz);
+    c->wall_sx = dalloc(c, N * tsz);
+    c->wall_sy = dalloc(c, N * tsz);
+    c->wall_flags = static_cast<uint8_t*>(dalloc(c, (size_t)c->nchunk * ny));
+    if (!c->wall_phie || !c->wall_sx || !c->wall_sy || !c->wall_flags)
+      return fail(c, LBM_ENOMEM, "wall fields");
+  }
+  if (u_wall && !c->wall_uwx) {
+    c->wall_uwx = dalloc(c, N * tsz);
+    c->wall_uwy = dalloc(c, N * tsz);
+    if (!c->wall_uwx || !c->wall_uwy) return fail(c, LBM_ENOMEM, "wall velocity");
+  }
+  Tmp stage(c, (size_t)N * 5 * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "wall staging");
+  double* d = stage.as<double>();
+  const double* src[4] = {phi_s, psi_r, psi_a, u_wall};
+  double* dst[4] = {d, d + N, d + 2 * N, d + 3 * N};
+  for (int k = 0; k < 4; ++k) {
+    if (!src[k]) continue;
+    CK(c, cudaMemcpyAsync(dst[k], src[k], (k == 3 ? 2 : 1) * N * sizeof(double),
+                          cudaMemcpyHostToDevice, c->stream));
+  }
+  void* uwx = u_wall ? c->wall_uwx : nullptr;
+  void* uwy = u_wall ? c->wall_uwy : nullptr;
+  cudaError_t e;
+  if (c->p.storage == LBM_FP64) {
+    auto f = c->Q == 9 ? launch_wall_prepare<9, double> : launch_wall_prepare<21, double>;
+    e = f(phi_s ? dst[0] : nullptr, psi_r ? dst[1] : nullptr, psi_a ? dst[2] : nullptr,
+          u_wall ? dst[3] : nullptr, G_R, G_A, epsilon, nx, ny, (double*)c->wall_phie,
+          (double*)c->wall_sx, (double*)c->wall_sy, (double*)uwx, (double*)uwy, c->wall_flags,
+          c->nchunk, c->stream);
+  } else {
+    auto f = c->Q == 9 ? launch_wall_prepare<9, float> : launch_wall_prepare<21, float>;
+    e = f(phi_s ? dst[0] : nullptr, psi_r ? dst[1] : nullptr, psi_a ? dst[2] : nullptr,
+          u_wall ? dst[3] : nullptr, G_R, G_A, epsilon, nx, ny, (float*)c->wall_phie,
+          (float*)c->wall_sx, (float*)c->wall_sy, (float*)uwx, (float*)uwy, c->wall_flags,
+          c->nchunk, c->stream);
+  }
+  CK(c, e);
+  if (!u_wall && c->wall_uwx) {
+    // keep the buffers but stop using them
+    dfree(c, c->wall_uwx);
+    dfree(c, c->wall_uwy);
+    c->wall_uwx = c->wall_uwy = nullptr;
+  }
+  c->has_wall = phi_s || psi_r || psi_a;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!f) return fail(c, LBM_EINVAL, "null populations");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  Tmp stage(c, (size_t)N * (c->Q + 1) * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "population staging");
+  double* d = stage.as<double>();
+  CK(c, cudaMemcpyAsync(d, f, (size_t)N * c->Q * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_colsum(d, c->Q, N, d + (int64_t)c->Q * N, c->stream));
+  rc = set_shift_from_rho(c, d + (int64_t)c->Q * N);
+  if (rc) return rc;
+  rc = dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+    CK(c, launch_encode<Q, S>(d, static_cast<S*>(c->buf[c->cur]), c->p.nx, c->p.ny, c->pitch,
+                              c->plane, c->rho_s, c->stream));
+    return LBM_OK;
+  });
+  if (rc) return rc;
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->has_state = true;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_set_equilibrium(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                        const double* dfi) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!rho || !ux || !uy) return fail(c, LBM_EINVAL, "null rho/ux/uy");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  const int64_t extra = dfi ? (int64_t)c->Q * N : 0;
+  Tmp stage(c, (size_t)(3 * N + extra) * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "equilibrium staging");
+  double* d = stage.as<double>();
+  CK(c, cudaMemcpyAsync(d, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(d + N, ux, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(d + 2 * N, uy, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (dfi)
+    CK(c, cudaMemcpyAsync(d + 3 * N, dfi, extra * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  rc = set_shift_from_rho(c, d);
+  if (rc) return rc;
+  rc = dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+    CK(c, launch_equilibrium<Q, S>(d, d + N, d + 2 * N, dfi ? d + 3 * N : nullptr,
+                                   static_cast<S*>(c->buf[c->cur]), c->p.nx, c->p.ny, c->pitch,
+                                   c->plane, c->rho_s, c->stream));
+    return LBM_OK;
+  });
+  if (rc) return rc;
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->has_state = true;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+static int read_status(lbm_ctx* c) {
+  uint32_t h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (h & kStatusTimeout)
+    return fail(c, LBM_ETIMEOUT, "a TMA stage wait timed out in the step kernel");
+  if (h & kStatusNonFinite)
+    return fail(c, LBM_ENONFINITE, "non-finite density after %lld steps", (long long)c->steps);
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(c, LBM_EINVAL, "negative step count");
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    rc = dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+      return run_pass<Q, S>(c, kModeStep, nullptr, nullptr, nullptr, 0,
+                            static_cast<S*>(c->buf[c->cur ^ 1]));
+    });
+    if (rc) return rc;
+    c->cur ^= 1;
+    c->steps += 1;
+    if (c->p.check_every > 0 && c->steps % c->p.check_every == 0) {
+      rc = read_status(c);
+      if (rc) return rc;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_moments_device(lbm_ctx* c, double* d_rho, double* d_ux, double* d_uy) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  // The read-out pass writes all three arrays; route unwanted ones to scratch.
+  Tmp scratch(c, (!d_rho || !d_ux || !d_uy) ? (size_t)N * sizeof(double) : 0);
+  double* sink = scratch.as<double>();
+  if ((!d_rho || !d_ux || !d_uy) && !sink) return fail(c, LBM_ENOMEM, "moments scratch");
+  return dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+    return run_pass<Q, S>(c, kModeMoments, d_rho ? d_rho : sink, d_ux ? d_ux : sink,
+                          d_uy ? d_uy : sink, 0, nullptr);
+  });
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  Tmp stage(c, (size_t)3 * N * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "moments staging");
+  double* d = stage.as<double>();
+  rc = lbm_moments_device(c, d, d + N, d + 2 * N);
+  if (rc) return rc;
+  double* hs[3] = {rho, ux, uy};
+  for (int k = 0; k < 3; ++k)
+    if (hs[k])
+      CK(c, cudaMemcpyAsync(hs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!f) return fail(c, LBM_EINVAL, "null output");
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  Tmp stage(c, (size_t)N * c->Q * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "population staging");
+  double* d = stage.as<double>();
+  rc = dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+    CK(c, launch_decode<Q, S>(static_cast<const S*>(c->buf[c->cur]), d, c->p.nx, c->p.ny,
+                              c->pitch, c->plane, c->rho_s, c->stream));
+    return LBM_OK;
+  });
+  if (rc) return rc;
+  CK(c, cudaMemcpyAsync(f, d, (size_t)N * c->Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_totals(lbm_ctx* c, double out[3]) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!out) return fail(c, LBM_EINVAL, "null output");
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  const int64_t N = (int64_t)c->p.nx * c->p.ny;
+  Tmp stage(c, (size_t)3 * N * sizeof(double));
+  if (!stage.p) return fail(c, LBM_ENOMEM, "totals staging");
+  double* d = stage.as<double>();
+  rc = dispatch(c->Q, c->p.storage, [&]<int Q, typename S>() -> int {
+    return run_pass<Q, S>(c, kModeMoments, d, d + N, d + 2 * N, 1, nullptr);
+  });
+  if (rc) return rc;
+  CK(c, launch_reduce3(d, d + N, d + 2 * N, N, c->d_partials, c->nparts, c->d_out3, c->stream));
+  CK(c, cudaMemcpyAsync(out, c->d_out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_steps_done(const lbm_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(nullptr, LBM_EINVAL, "null argument");
+  *out = c->steps;
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+  int rc = guard(c);
+  if (rc) return rc;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+int lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaGetLastError();
+  std::vector<void*> live = c->owned;
+  for (void* p : live) dfree(c, p);
+  delete c;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+int lbm_get_layout(const lbm_ctx* c, lbm_layout* out) {
+  if (!c || !out) return fail(nullptr, LBM_EINVAL, "null argument");
+  out->bytes_per_node = 2LL * c->Q * c->esize;
+  out->pitch = c->pitch;
+  out->strip_width = c->W;
+  out->tile_rows = c->tile_rows;
+  out->grid_x = c->grid_x;
+  out->grid_y = c->grid_y;
+  out->stages = c->NS;
+  out->ghost_x = c->GX;
+  out->ghost_y = c->GY;
+  out->device_bytes = 2LL * c->plane * c->Q * c->esize;
+  return LBM_OK;
+}
+
+int lbm_wall_gaussian_filter(int32_t nx, int32_t ny, int32_t lattice, const uint8_t* solid,
+                             int32_t n_rep, int32_t n_att, double* phi_s, double* psi_r,
+                             double* psi_a) {
+  if (nx < 1 || ny < 1 || !solid || n_rep < 0 || n_att < n_rep ||
+      (lattice != LBM_D2Q9 && lattice != LBM_D2Q21))
+    return fail(nullptr, LBM_EINVAL, "wall filter arguments");
+  const int64_t N = (int64_t)nx * ny;
+  double* g[2] = {nullptr, nullptr};
+  double* keep = nullptr;
+  uint8_t* dsolid = nullptr;
+  auto cleanup = [&] {
+    cudaFree(g[0]);
+    cudaFree(g[1]);
+    cudaFree(keep);
+    cudaFree(dsolid);
+  };
+  if (cudaMalloc(&g[0], N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&g[1], N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&keep, N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dsolid, N) != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return fail(nullptr, LBM_ENOMEM, "wall filter buffers");
+  }
+  std::vector<double> h0(N);
+  for (int64_t n = 0; n < N; ++n) h0[n] = solid[n] ? 1.0 : 0.0;
+  cudaError_t e = cudaMemcpy(g[0], h0.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dsolid, solid, N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_rep == 0) e = cudaMemcpy(keep, g[0], N * sizeof(double), cudaMemcpyDeviceToDevice);
+  int cur = 0;
+  for (int it = 1; it <= n_att && e == cudaSuccess; ++it) {
+    e = launch_filter_pass(lattice, g[cur], g[cur ^ 1], dsolid, nx, ny, nullptr);
+    cur ^= 1;
+    if (e == cudaSuccess && it == n_rep)
+      e = cudaMemcpy(keep, g[cur], N * sizeof(double), cudaMemcpyDeviceToDevice);
+  }
+  std::vector<double> ga(N), gr(N);
+  if (e == cudaSuccess) e = cudaMemcpy(ga.data(), g[cur], N * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(gr.data(), keep, N * sizeof(double), cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "wall filter: %s", cudaGetErrorString(e));
+  for (int64_t n = 0; n < N; ++n) {
+    if (phi_s) phi_s[n] = ga[n];
+    if (psi_r) psi_r[n] = gr[n];
+    if (psi_a) psi_a[n] = ga[n] - gr[n];
+  }
+  return LBM_OK;
+}
+
+int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double* thickness,
+                       double core_lambda, double core_cut, double tail_exp, double tail_cut,
+                       double phi_cut, double* phi_s, double* psi_r, double* psi_a) {
+  if (nx < 1 || ny < 1 || !dist || !thickness || !(core_lambda > 0.0))
+    return fail(nullptr, LBM_EINVAL, "core/tail arguments");
+  const double rc = std::exp(-core_cut / core_lambda);
+  const double tc = std::pow(1.0 + tail_cut, -tail_exp);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int64_t n = (int64_t)y * nx + x;
+      const double d = dist[n], T = thickness[x];
+      double ph = 0.5 * (1.0 - std::tanh((d - 0.5 * T) / (0.25 * T)));
+      if (ph < phi_cut) ph = 0.0;
+      if (phi_s) phi_s[n] = ph;
+      if (psi_r) psi_r[n] = d < core_cut ? std::exp(-d / core_lambda) - rc : 0.0;
+      if (psi_a) psi_a[n] = d < tail_cut ? std::pow(1.0 + d, -tail_exp) - tc : 0.0;
+    }
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// Launch-side view of the kernels: per-(lattice, storage) shapes and the
+// host launchers that the engine dispatches to.  Each storage type's kernels
+// are compiled in their own translation unit (step_<type>.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+// CTA width and TMA pipeline depth per (lattice, storage).
+template <int Q, typename S> struct StepConfig {
+  static constexpr int W = 128;
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 6 : 8) : (sizeof(S) == 8 ? 5 : 6);
+};
+
+template <int Q, typename S>
+using ConfigShape = StepShape<Q, S, StepConfig<Q, S>::W, StepConfig<Q, S>::NS>;
+
+// Launches the fused step (mode kModeStep) or the read-out pass (kModeMoments).
+template <int Q, typename S>
+cudaError_t launch_step(const CUtensorMap& src, const StepArgs<typename Codec<S>::T, S>& a,
+                        dim3 grid, cudaStream_t stream, int mode);
+
+// CTAs of the step kernel that fit on one SM (occupancy query).
+template <int Q, typename S> int step_ctas_per_sm();
+
+// Auxiliary kernels (aux.cu).
+template <int Q, typename S>
+cudaError_t launch_encode(const double* f, S* buf, int nx, int ny, int64_t pitch, int64_t plane,
+                          double rho_s, cudaStream_t st);
+template <int Q, typename S>
+cudaError_t launch_equilibrium(const double* rho, const double* ux, const double* uy,
+                               const double* dfi, S* buf, int nx, int ny, int64_t pitch,
+                               int64_t plane, double rho_s, cudaStream_t st);
+template <int Q, typename S>
+cudaError_t launch_decode(const S* buf, double* f, int nx, int ny, int64_t pitch, int64_t plane,
+                          double rho_s, cudaStream_t st);
+template <int Q, typename T>
+cudaError_t launch_wall_prepare(const double* phi, const double* psr, const double* psa,
+                                const double* uw, double G_R, double G_A, double eps, int nx,
+                                int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint8_t* flags,
+                                int nchunk, cudaStream_t st);
+
+// Sum of rho_s candidates: sum_i f_i over all nodes of an FP64 [Q][N] array
+// (fsum) or of an [N] array (rho).  Deterministic two-pass Neumaier reduction.
+cudaError_t launch_reduce3(const double* a, const double* b, const double* c, int64_t n,
+                           double* partials, int nparts, double* out, cudaStream_t st);
+cudaError_t launch_colsum(const double* f, int q, int64_t n, double* out_n, cudaStream_t st);
+
+cudaError_t launch_filter_pass(int q, const double* g, double* out, const uint8_t* solid, int nx,
+                               int ny, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,239 @@
+// Per-node arithmetic of the wetting model (Sec. II of arXiv:1202.6130):
+// storage codecs, pseudo-potentials, second-order equilibrium, projection and
+// the exact-difference-method BGK collision.  Shared by the fused step kernel
+// and by the read-out kernels, so that moments are computed with exactly the
+// arithmetic the step uses.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Storage codecs.  FP64 / FP32 store f directly; FP16S / BF16S store the
+// deviation f_i - w_i rho_s rounded to nearest-even, and compute in FP32.
+// ---------------------------------------------------------------------------
+template <typename S> struct Codec;
+
+template <> struct Codec<double> {
+  using T = double;
+  static constexpr bool kShifted = false;
+  __device__ __forceinline__ static T dec(double v, T) { return v; }
+  __device__ __forceinline__ static double enc(T f, T) { return f; }
+};
+
+template <> struct Codec<float> {
+  using T = float;
+  static constexpr bool kShifted = false;
+  __device__ __forceinline__ static T dec(float v, T) { return v; }
+  __device__ __forceinline__ static float enc(T f, T) { return f; }
+};
+
+template <> struct Codec<__half> {
+  using T = float;
+  static constexpr bool kShifted = true;
+  __device__ __forceinline__ static T dec(__half v, T wrs) { return __half2float(v) + wrs; }
+  __device__ __forceinline__ static __half enc(T f, T wrs) { return __float2half_rn(f - wrs); }
+};
+
+template <> struct Codec<__nv_bfloat16> {
+  using T = float;
+  static constexpr bool kShifted = true;
+  __device__ __forceinline__ static T dec(__nv_bfloat16 v, T wrs) {
+    return __bfloat162float(v) + wrs;
+  }
+  __device__ __forceinline__ static __nv_bfloat16 enc(T f, T wrs) {
+    return __float2bfloat16_rn(f - wrs);
+  }
+};
+
+// Ghost widths of the padded population layout.  x: at least 2R columns (the
+// halo node's own pull) rounded up to 16 bytes so that every TMA box starts
+// on a 16-byte boundary; y: 2R rows.
+template <typename S, int R> __host__ __device__ constexpr int ghost_x() {
+  return ((2 * R * (int)sizeof(S) + 15) / 16) * 16 / (int)sizeof(S);
+}
+template <int R> __host__ __device__ constexpr int ghost_y() { return 2 * R; }
+
+// ---------------------------------------------------------------------------
+// Run-time parameters of the update (compute precision T).
+// ---------------------------------------------------------------------------
+template <typename T> struct Physics {
+  T omega;           // 1 / tau
+  T one_m_omega;     // 1 - 1 / tau
+  T G;               // fluid-fluid coupling in F_FF = -G psi sum w psi r
+  T rho0;            // exponential psi scale
+  T eos_tv, eos_tu, eos_tl, eos_r1, eos_r2, eos_p1, eos_p2;
+  T bfx, bfy;        // body-force density
+  T rho_s;           // FP16S / BF16S shift
+  int32_t psi_kind;  // 0 exp, 1 EOS
+  int32_t project;   // projection step on/off
+};
+
+template <typename T> struct WallFields {
+  const T* phie;          // phi_S^epsilon            [ny][nx]
+  const T* sx;            // S = sum_i w_i psi_FS(x + r_i) r_i
+  const T* sy;
+  const T* uwx;           // wall velocity (nullable)
+  const T* uwy;
+  const uint8_t* flags;   // [ny][nchunk]: 1 if any wall term is non-zero in the 32-column chunk
+  int32_t nchunk;
+  int32_t active;         // 0: no wall at all
+};
+
+template <typename T> __device__ __forceinline__ T t_exp(T v);
+template <> __device__ __forceinline__ double t_exp<double>(double v) { return exp(v); }
+template <> __device__ __forceinline__ float t_exp<float>(float v) { return expf(v); }
+template <typename T> __device__ __forceinline__ T t_sqrt(T v);
+template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
+
+// psi(rho): exponential (Shan-Chen) or sqrt(2 [rho theta - p_EOS(rho)]) with the
+// piecewise-linear Eq. EOS.
+template <int Q, typename T>
+__device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
+  if (P.psi_kind == 0) {
+    return P.rho0 * (T(1) - t_exp<T>(-rho / P.rho0));
+  }
+  constexpr T theta = T(Lattice<Q>::THETA);
+  T p;
+  if (rho <= P.eos_r1)
+    p = rho * P.eos_tv;
+  else if (rho <= P.eos_r2)
+    p = P.eos_p1 + (rho - P.eos_r1) * P.eos_tu;
+  else
+    p = P.eos_p2 + (rho - P.eos_r2) * P.eos_tl;
+  T arg = T(2) * (rho * theta - p);
+  return t_sqrt<T>(arg > T(0) ? arg : T(0));
+}
+
+// Exact reciprocal constants of the equilibrium for each lattice.
+template <int Q> struct EqConst;
+template <> struct EqConst<9> {
+  static constexpr double inv_theta = 3.0, inv_2theta2 = 4.5, inv_2theta = 1.5;
+};
+template <> struct EqConst<21> {
+  static constexpr double inv_theta = 1.5, inv_2theta2 = 1.125, inv_2theta = 0.75;
+};
+
+// f_i^eq = w_i rho [1 + c.u / theta + (c.u)^2 / (2 theta^2) - u^2 / (2 theta)]
+template <int Q, typename T>
+__device__ __forceinline__ T feq(int i, T rho, T ux, T uy, T usq_term) {
+  using L = Lattice<Q>;
+  using E = EqConst<Q>;
+  const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
+  return T(L::w(i)) * rho * (T(1) + cu * T(E::inv_theta) + cu * cu * T(E::inv_2theta2) - usq_term);
+}
+
+// Projection step (Sec. II, after Eq. f2): f_i <- w_i [rho + j.c_i / theta
+//   + (Pi - rho theta I):(c_i c_i - theta I) / (2 theta^2)], Pi = sum f c c.
+template <int Q, typename T>
+__device__ __forceinline__ void project(T (&f)[Q], T rho, T jx, T jy) {
+  using L = Lattice<Q>;
+  using E = EqConst<Q>;
+  constexpr T theta = T(L::THETA);
+  T pxx = 0, pxy = 0, pyy = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const T cx = T(L::cx(i)), cy = T(L::cy(i));
+    pxx += f[i] * (cx * cx);
+    pxy += f[i] * (cx * cy);
+    pyy += f[i] * (cy * cy);
+  }
+  const T axx = pxx - rho * theta, ayy = pyy - rho * theta;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const T cx = T(L::cx(i)), cy = T(L::cy(i));
+    const T contr = axx * (cx * cx - theta) + T(2) * pxy * (cx * cy) + ayy * (cy * cy - theta);
+    f[i] = T(L::w(i)) * (rho + (jx * cx + jy * cy) * T(E::inv_theta) + contr * T(E::inv_2theta2));
+  }
+}
+
+// a / b: FP64 divides (the oracle's rounding); FP32 multiplies by a reciprocal
+// computed once per node.
+template <typename T> __device__ __forceinline__ T div_rho(T a, T b, T inv_b);
+template <> __device__ __forceinline__ double div_rho<double>(double a, double b, double) {
+  return a / b;
+}
+template <> __device__ __forceinline__ float div_rho<float>(float a, float, float inv_b) {
+  return a * inv_b;
+}
+
+// rho and j in table order.
+template <int Q, typename T>
+__device__ __forceinline__ void node_moments(const T (&f)[Q], T& rho, T& jx, T& jy) {
+  using L = Lattice<Q>;
+  rho = f[0];
+  jx = T(L::cx(0)) * f[0];
+  jy = T(L::cy(0)) * f[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    rho += f[i];
+    if (L::cx(i) == 1) jx += f[i];
+    else if (L::cx(i) == -1) jx -= f[i];
+    else if (L::cx(i) != 0) jx += T(L::cx(i)) * f[i];
+    if (L::cy(i) == 1) jy += f[i];
+    else if (L::cy(i) == -1) jy -= f[i];
+    else if (L::cy(i) != 0) jy += T(L::cy(i)) * f[i];
+  }
+}
+
+// Total force on a node (Eqs. force_SC, force_SC_FS, wall_shift):
+//   F = F_FF + rho S + rho phi^eps (U_wall - u - F_FF / rho) + body force.
+// sfx, sfy: sum_i w_i psi(x + r_i) r_i; wall terms only when has_wall.
+template <typename T>
+__device__ __forceinline__ void node_force(const Physics<T>& P, T rho, T ux, T uy, T psi_c,
+                                           T sfx, T sfy, bool has_wall, T phie, T Sx, T Sy,
+                                           T uwx, T uwy, T inv_rho, T& Fx, T& Fy) {
+  const T mg = -P.G * psi_c;
+  const T ffx = mg * sfx;
+  const T ffy = mg * sfy;
+  Fx = ffx;
+  Fy = ffy;
+  if (has_wall) {
+    const T flx = rho * Sx, fly = rho * Sy;
+    const T rp = rho * phie;
+    const T dfx = rp * (uwx - ux - div_rho<T>(ffx, rho, inv_rho));
+    const T dfy = rp * (uwy - uy - div_rho<T>(ffy, rho, inv_rho));
+    Fx = ((ffx + flx) + dfx);
+    Fy = ((ffy + fly) + dfy);
+  }
+  Fx += P.bfx;
+  Fy += P.bfy;
+}
+
+// EDM-BGK collision: f_post = f^eq(rho, u*) + (1 - 1/tau) (f - f^eq(rho, u)),
+// which is f - (f - f^eq(u)) / tau + [f^eq(u*) - f^eq(u)] rearranged.
+//
+// With FP32 arithmetic the rest population is taken from the mass balance
+// sum_i f_i^post = rho, which the update satisfies identically: evaluating
+// every f^eq_i in single precision otherwise leaves a rounding bias in the
+// node's mass (of order 1e-7 rho per step, correlated in space and time) that
+// accumulates into a visible density drift at interfaces.
+template <int Q, typename T>
+__device__ __forceinline__ void node_collide(const Physics<T>& P, T (&f)[Q], T rho, T ux, T uy,
+                                             T usx, T usy) {
+  using E = EqConst<Q>;
+  using L = Lattice<Q>;
+  const T usq0 = (ux * ux + uy * uy) * T(E::inv_2theta);
+  const T usq1 = (usx * usx + usy * usy) * T(E::inv_2theta);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const T e0 = feq<Q, T>(i, rho, ux, uy, usq0);
+    const T e1 = feq<Q, T>(i, rho, usx, usy, usq1);
+    f[i] = e1 + P.one_m_omega * (f[i] - e0);
+  }
+  if constexpr (sizeof(T) == 4) {
+    T moving = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if (i != L::REST) moving += f[i];
+    f[L::REST] = rho - moving;
+  }
+}
+
+}  // namespace lbm
