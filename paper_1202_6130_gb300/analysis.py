@@ -1,0 +1,162 @@
+"""Host-side FP64 measurements on the engine's moment fields (Sec. III of
+arXiv:1202.6130): the static contact angle by a least-squares circle fit in the
+hydrodynamic region, the hydrodynamic slip of a pressure-driven channel flow,
+the Laplace pressure jump of a drop, and spurious-current magnitude.
+
+These read outputs of ``Simulation.moments()``; they are not part of the time
+step.  Conventions: arrays [y][x], the solid slab across the periodic seam
+near y = 0, wall probability phi_S; the hydrodynamic region is phi_S < 0.01 and
+the solid surface is the line phi_S = 0.5.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def contour_points(field: np.ndarray, level: float, mask: np.ndarray | None = None):
+    """Points where ``field`` crosses ``level`` between horizontally or vertically
+    adjacent nodes (linear interpolation), optionally only between nodes that are
+    both inside ``mask``.  Returns (x, y) arrays (non-periodic: no wrap)."""
+    f = field - level
+    xs, ys = [], []
+    # horizontal neighbours
+    a, b = f[:, :-1], f[:, 1:]
+    cross = (a * b < 0)
+    if mask is not None:
+        cross &= mask[:, :-1] & mask[:, 1:]
+    yy, xx = np.nonzero(cross)
+    t = a[yy, xx] / (a[yy, xx] - b[yy, xx])
+    xs.append(xx + t)
+    ys.append(yy.astype(float))
+    # vertical neighbours
+    a, b = f[:-1, :], f[1:, :]
+    cross = (a * b < 0)
+    if mask is not None:
+        cross &= mask[:-1, :] & mask[1:, :]
+    yy, xx = np.nonzero(cross)
+    t = a[yy, xx] / (a[yy, xx] - b[yy, xx])
+    xs.append(xx.astype(float))
+    ys.append(yy + t)
+    return np.concatenate(xs), np.concatenate(ys)
+
+
+def fit_circle(x: np.ndarray, y: np.ndarray, iterations: int = 50):
+    """Least-squares circle: algebraic (Kasa) start, then Gauss-Newton on the
+    geometric distances.  Returns (xc, yc, R)."""
+    A = np.column_stack([x, y, np.ones_like(x)])
+    rhs = x * x + y * y
+    (a, b, c), *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    xc, yc = a / 2.0, b / 2.0
+    R = math.sqrt(max(c + xc * xc + yc * yc, 1e-300))
+    for _ in range(iterations):
+        dx, dy = x - xc, y - yc
+        d = np.sqrt(dx * dx + dy * dy)
+        d = np.where(d == 0, 1e-300, d)
+        res = d - R
+        J = np.column_stack([-dx / d, -dy / d, -np.ones_like(d)])
+        step, *_ = np.linalg.lstsq(J, -res, rcond=None)
+        xc, yc, R = xc + step[0], yc + step[1], R + step[2]
+        if np.max(np.abs(step)) < 1e-12:
+            break
+    return float(xc), float(yc), float(R)
+
+
+def surface_line(phi_col: np.ndarray, level: float = 0.5) -> float:
+    """Height above the bottom solid row where phi_S falls through ``level``
+    (first crossing going up from y = 0; linear interpolation)."""
+    for y in range(1, len(phi_col)):
+        if phi_col[y] <= level < phi_col[y - 1]:
+            return (y - 1) + (phi_col[y - 1] - level) / (phi_col[y - 1] - phi_col[y])
+    return 0.0
+
+
+@dataclass
+class ContactAngle:
+    theta_deg: float
+    xc: float
+    yc: float
+    R: float
+    y_base: float
+    npoints: int
+
+
+def contact_angle(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
+                  x_range=None, y_max=None) -> ContactAngle:
+    """Static contact angle of a drop resting on the bottom wall.
+
+    The drop's interface is the contour rho = (rho_l + rho_v)/2; only points in
+    the hydrodynamic region (phi_S < 0.01) above the bottom wall and below
+    ``y_max`` (default ny/2) are fitted.  theta = acos((y_b - y_c)/R) with y_b the
+    solid surface (phi_S = 0.5), i.e. acos(1 - h/R) with h the apex height above
+    y_b (Sec. III, static wetting)."""
+    ny, nx = rho.shape
+    y_max = ny // 2 if y_max is None else y_max
+    mask = phi_s < 0.01
+    mask[y_max:, :] = False
+    if x_range is not None:
+        m2 = np.zeros_like(mask)
+        m2[:, x_range[0]:x_range[1]] = True
+        mask &= m2
+    x, y = contour_points(rho, 0.5 * (rho_l + rho_v), mask)
+    if len(x) < 5:
+        raise ValueError("too few interface points in the hydrodynamic region")
+    xc, yc, R = fit_circle(x, y)
+    col = phi_s[:, int(round(xc)) % nx]
+    yb = surface_line(col, 0.5)
+    c = max(-1.0, min(1.0, (yb - yc) / R))
+    return ContactAngle(math.degrees(math.acos(c)), xc, yc, R, yb, len(x))
+
+
+@dataclass
+class Slip:
+    slip_length: float
+    y_w: float
+    u_wall: float
+    du_wall: float
+    curvature: float
+
+
+def slip_length(ux: np.ndarray, phi_s: np.ndarray) -> Slip:
+    """Hydrodynamic slip of a body-force-driven channel (Sec. III, Poiseuille):
+    fit u(y) = a y^2 + b y + c over the hydrodynamic region (phi_S < 0.01) of the
+    x-averaged profile; the boundary y_w is where phi_S falls through 0.01 above
+    the bottom wall; slip length = u(y_w) / |u'(y_w)|."""
+    u = ux.mean(axis=1)
+    phi = phi_s.mean(axis=1)
+    ny = len(u)
+    bulk = phi < 0.01
+    ys = np.arange(ny, dtype=float)
+    a, b, c = np.polyfit(ys[bulk], u[bulk], 2)
+    yw = surface_line(phi, 0.01)
+    uw = a * yw * yw + b * yw + c
+    du = 2 * a * yw + b
+    return Slip(float(uw / abs(du)) if du != 0 else float("inf"), float(yw), float(uw),
+                float(du), float(2 * a))
+
+
+def pressure_exp(rho: np.ndarray, G: float, rho0: float = 1.0, theta: float = 1.0 / 3.0):
+    """Bulk pressure of the exponential pseudo-potential fluid:
+    p = rho theta + G theta psi^2 / 2 (the continuum limit of Eq. force_SC)."""
+    psi = rho0 * (1.0 - np.exp(-rho / rho0))
+    return rho * theta + 0.5 * G * theta * psi * psi
+
+
+def laplace_jump(rho: np.ndarray, G: float, center, r_in: float, r_out: float,
+                 rho0: float = 1.0, theta: float = 1.0 / 3.0):
+    """Pressure inside (r < r_in) minus outside (r > r_out) of a drop centred at
+    ``center`` on the periodic lattice."""
+    ny, nx = rho.shape
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    dx = (x - center[0] + nx / 2) % nx - nx / 2
+    dy = (y - center[1] + ny / 2) % ny - ny / 2
+    r = np.hypot(dx, dy)
+    p = pressure_exp(rho, G, rho0, theta)
+    return float(p[r < r_in].mean() - p[r > r_out].mean())
+
+
+def spurious_current(ux: np.ndarray, uy: np.ndarray) -> float:
+    """max |u| over the lattice."""
+    return float(np.sqrt(ux * ux + uy * uy).max())

@@ -46,13 +46,13 @@ __global__ void encode_kernel(const double* __restrict__ f, S* __restrict__ buf,
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
   const int64_t N = (int64_t)nx * ny;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
     const int xs = wrap(x + L::cx(i), nx), ys = wrap(y + L::cy(i), ny);
     const double v = f[i * N + (int64_t)ys * nx + xs];
     const S e = Codec<S>::enc((T)v, (T)(L::w(i) * rho_s));
-    store_images<S, GX, GY>(buf, plane, pitch, i, x, y, nx, ny, e);
-  }
+    store_images<S, GX, GY>(buf, plane, pitch, Planes<Q>::template plane<i>, x, y, nx, ny, e);
+  });
 }
 
 template <int Q, typename S>
@@ -69,16 +69,16 @@ __global__ void equilibrium_kernel(const double* __restrict__ rho, const double*
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
   const int64_t N = (int64_t)nx * ny;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
     const int64_t m = (int64_t)wrap(y + L::cy(i), ny) * nx + wrap(x + L::cx(i), nx);
     const double r = rho[m], vx = ux[m], vy = uy[m];
     const double usq = (vx * vx + vy * vy) * E::inv_2theta;
     double v = feq<Q, double>(i, r, vx, vy, usq);
     if (dfi) v = v + dfi[i * N + m];
     const S e = Codec<S>::enc((T)v, (T)(L::w(i) * rho_s));
-    store_images<S, GX, GY>(buf, plane, pitch, i, x, y, nx, ny, e);
-  }
+    store_images<S, GX, GY>(buf, plane, pitch, Planes<Q>::template plane<i>, x, y, nx, ny, e);
+  });
 }
 
 template <int Q, typename S>
@@ -92,12 +92,13 @@ __global__ void decode_kernel(const S* __restrict__ buf, double* __restrict__ f,
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
   const int64_t N = (int64_t)nx * ny;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
     // f_i(x) = P_i(x - c_i); the ghost frame makes the source in-bounds.
-    const int64_t src = i * plane + (int64_t)(y - L::cy(i) + GY) * pitch + (x - L::cx(i) + GX);
+    const int64_t src = Planes<Q>::template plane<i> * plane +
+                        (int64_t)(y - L::cy(i) + GY) * pitch + (x - L::cx(i) + GX);
     f[i * N + n] = (double)Codec<S>::dec(buf[src], (T)(L::w(i) * rho_s));
-  }
+  });
 }
 
 // phi_S^eps, S(x) = sum_i w_i psi_FS(x + r_i) r_i with psi_FS = G_A psi_A - G_R psi_R
@@ -134,15 +135,16 @@ __global__ void wall_prepare_kernel(const double* __restrict__ phi, const double
   }
 }
 
-// flags[y][c] = 1 when any of phi^eps, S_x, S_y is non-zero in columns 32c..32c+31.
+// flags[y][c] = 1 when any of phi^eps, S_x, S_y is non-zero in columns
+// 32c..32c+31 (0 in the padding chunks past nx).
 template <typename T>
 __global__ void wall_flags_kernel(const T* __restrict__ phie, const T* __restrict__ sx,
-                                  const T* __restrict__ sy, int nx, int ny, int nchunk,
-                                  uint8_t* __restrict__ flags) {
+                                  const T* __restrict__ sy, int nx, int ny, int nchunk_pad,
+                                  uint32_t* __restrict__ flags) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nchunk * ny) return;
-  const int y = (int)(t / nchunk), c = (int)(t % nchunk);
-  uint8_t any = 0;
+  if (t >= (int64_t)nchunk_pad * ny) return;
+  const int y = (int)(t / nchunk_pad), c = (int)(t % nchunk_pad);
+  uint32_t any = 0;
   for (int x = 32 * c; x < min(nx, 32 * c + 32); ++x) {
     const int64_t n = (int64_t)y * nx + x;
     if (phie[n] != T(0) || sx[n] != T(0) || sy[n] != T(0)) any = 1;
@@ -267,15 +269,15 @@ cudaError_t launch_decode(const S* buf, double* f, int nx, int ny, int64_t pitch
 template <int Q, typename T>
 cudaError_t launch_wall_prepare(const double* phi, const double* psr, const double* psa,
                                 const double* uw, double G_R, double G_A, double eps, int nx,
-                                int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint8_t* flags,
-                                int nchunk, cudaStream_t st) {
+                                int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint32_t* flags,
+                                int nchunk_pad, cudaStream_t st) {
   const int64_t N = (int64_t)nx * ny;
   wall_prepare_kernel<Q, T><<<blocks_for(N), kThreads, 0, st>>>(phi, psr, psa, uw, G_R, G_A, eps,
                                                                 nx, ny, phie, sx, sy, uwx, uwy);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wall_flags_kernel<T><<<blocks_for((int64_t)nchunk * ny), kThreads, 0, st>>>(phie, sx, sy, nx, ny,
-                                                                              nchunk, flags);
+  wall_flags_kernel<T><<<blocks_for((int64_t)nchunk_pad * ny), kThreads, 0, st>>>(
+      phie, sx, sy, nx, ny, nchunk_pad, flags);
   return cudaGetLastError();
 }
 
@@ -324,7 +326,7 @@ LBM_INSTANTIATE_AUX(21, __nv_bfloat16)
 #define LBM_INSTANTIATE_WALL(Q, T)                                                            \
   template cudaError_t launch_wall_prepare<Q, T>(const double*, const double*, const double*, \
                                                  const double*, double, double, double, int,  \
-                                                 int, T*, T*, T*, T*, T*, uint8_t*, int,       \
+                                                 int, T*, T*, T*, T*, T*, uint32_t*, int,      \
                                                  cudaStream_t);
 LBM_INSTANTIATE_WALL(9, double)
 LBM_INSTANTIATE_WALL(9, float)

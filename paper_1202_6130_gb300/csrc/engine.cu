@@ -33,8 +33,9 @@ struct lbm_ctx {
   void* wall_sy = nullptr;
   void* wall_uwx = nullptr;
   void* wall_uwy = nullptr;
-  uint8_t* wall_flags = nullptr;
-  int nchunk = 0;
+  uint32_t* wall_flags = nullptr;  // [ny][nchunk_pad]
+  int nchunk_pad = 0;
+  CUtensorMap flag_map;
   bool has_wall = false;
   uint32_t* d_status = nullptr;
   double* d_partials = nullptr;
@@ -168,7 +169,7 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
   cuuint64_t dims[3] = {(cuuint64_t)(c->p.nx + 2 * Sh::GX), (cuuint64_t)c->rows, (cuuint64_t)Q};
   cuuint64_t strides[2] = {(cuuint64_t)(c->pitch * sizeof(S)),
                            (cuuint64_t)(c->plane * sizeof(S))};
-  cuuint32_t box[3] = {(cuuint32_t)Sh::BW, 1, 1};
+  cuuint32_t box[3] = {(cuuint32_t)Sh::BW, 1, (cuuint32_t)Sh::BD};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(&c->tmap[which], tma_type<S>(), 3, c->buf[which], dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -244,6 +245,7 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   P.one_m_omega = (T)(1.0 - 1.0 / p.tau);
   P.G = (T)p.G;
   P.rho0 = (T)p.rho0;
+  P.inv_rho0 = (T)(1.0 / p.rho0);
   P.eos_tv = (T)p.eos_theta_v;
   P.eos_tu = (T)p.eos_theta_u;
   P.eos_tl = (T)p.eos_theta_l;
@@ -272,8 +274,6 @@ int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, in
   a.wall.sy = static_cast<const T*>(c->wall_sy);
   a.wall.uwx = static_cast<const T*>(c->wall_uwx);
   a.wall.uwy = static_cast<const T*>(c->wall_uwy);
-  a.wall.flags = c->wall_flags;
-  a.wall.nchunk = c->nchunk;
   a.wall.active = c->has_wall ? 1 : 0;
   a.nx = c->p.nx;
   a.ny = c->p.ny;
@@ -286,7 +286,9 @@ int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, in
   a.out_uy = o_uy;
   a.momentum = momentum;
   a.status = c->d_status;
-  CK(c, launch_step<Q, S>(c->tmap[c->cur], a, dim3(c->grid_x, c->grid_y), c->stream, mode));
+  // Without walls the flag map is never read; the population map stands in.
+  const CUtensorMap& fm = c->has_wall ? c->flag_map : c->tmap[c->cur];
+  CK(c, launch_step<Q, S>(c->tmap[c->cur], fm, a, dim3(c->grid_x, c->grid_y), c->stream, mode));
   return LBM_OK;
 }
 
@@ -408,13 +410,25 @@ int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const dou
   const int64_t N = (int64_t)nx * ny;
   const size_t tsz = c->p.storage == LBM_FP64 ? sizeof(double) : sizeof(float);
   if (!c->wall_phie) {
-    c->nchunk = (nx + 31) / 32;
+    // one uint32 flag per (row, 32-column chunk); rows padded to 16 bytes so
+    // that each strip's flag words are one aligned TMA box
+    c->nchunk_pad = ((nx + 31) / 32 + 3) / 4 * 4;
     c->wall_phie = dalloc(c, N * tsz);
     c->wall_sx = dalloc(c, N * tsz);
     c->wall_sy = dalloc(c, N * tsz);
-    c->wall_flags = static_cast<uint8_t*>(dalloc(c, (size_t)c->nchunk * ny));
+    c->wall_flags = static_cast<uint32_t*>(dalloc(c, (size_t)c->nchunk_pad * ny * 4));
     if (!c->wall_phie || !c->wall_sx || !c->wall_sy || !c->wall_flags)
       return fail(c, LBM_ENOMEM, "wall fields");
+    EncodeFn enc = get_encode();
+    if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)c->nchunk_pad, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)c->nchunk_pad * 4};
+    cuuint32_t box[2] = {(cuuint32_t)(c->W / 32), 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&c->flag_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, c->wall_flags, dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "flag tensor map (%d)", (int)r);
   }
   if (u_wall && !c->wall_uwx) {
     c->wall_uwx = dalloc(c, N * tsz);
@@ -439,13 +453,13 @@ int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const dou
     e = f(phi_s ? dst[0] : nullptr, psi_r ? dst[1] : nullptr, psi_a ? dst[2] : nullptr,
           u_wall ? dst[3] : nullptr, G_R, G_A, epsilon, nx, ny, (double*)c->wall_phie,
           (double*)c->wall_sx, (double*)c->wall_sy, (double*)uwx, (double*)uwy, c->wall_flags,
-          c->nchunk, c->stream);
+          c->nchunk_pad, c->stream);
   } else {
     auto f = c->Q == 9 ? launch_wall_prepare<9, float> : launch_wall_prepare<21, float>;
     e = f(phi_s ? dst[0] : nullptr, psi_r ? dst[1] : nullptr, psi_a ? dst[2] : nullptr,
           u_wall ? dst[3] : nullptr, G_R, G_A, epsilon, nx, ny, (float*)c->wall_phie,
           (float*)c->wall_sx, (float*)c->wall_sy, (float*)uwx, (float*)uwy, c->wall_flags,
-          c->nchunk, c->stream);
+          c->nchunk_pad, c->stream);
   }
   CK(c, e);
   if (!u_wall && c->wall_uwx) {

@@ -48,4 +48,27 @@ template <> struct Lattice<21> {
   }
 };
 
+// Device plane order of the populations: grouped by c_y (ascending), table
+// order inside a group.  The populations of one group pull from the same
+// source row, so their rows arrive in one TMA box of depth group_size.
+template <int Q> struct Planes {
+  using L = Lattice<Q>;
+  struct Table {
+    int plane[Q];  // plane of population i
+  };
+  static constexpr Table make() {
+    Table t{};
+    for (int i = 0; i < Q; ++i) {
+      int p = 0;
+      for (int j = 0; j < Q; ++j)
+        if (L::cy(j) < L::cy(i) || (L::cy(j) == L::cy(i) && j < i)) ++p;
+      t.plane[i] = p;
+    }
+    return t;
+  }
+  static constexpr Table kTable = make();
+  // Use only in constant expressions (template arguments, constexpr locals).
+  template <int I> static constexpr int plane = kTable.plane[I];
+};
+
 }  // namespace lbm

@@ -10,10 +10,15 @@
 
 namespace lbm {
 
-// CTA width and TMA pipeline depth per (lattice, storage).
+// CTA width, TMA pipeline depth and the CTAs per SM the register budget is
+// sized for, per (lattice, storage).  Shared memory per CTA is
+// NS * (Q box slots + flag slot) + the psi ring.
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
-  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 6 : 8) : (sizeof(S) == 8 ? 5 : 6);
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 5 : 6))
+                                     : (sizeof(S) == 8 ? 5 : 6);
+  static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 6 : 8))
+                                       : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3));
 };
 
 template <int Q, typename S>
@@ -21,8 +26,9 @@ using ConfigShape = StepShape<Q, S, StepConfig<Q, S>::W, StepConfig<Q, S>::NS>;
 
 // Launches the fused step (mode kModeStep) or the read-out pass (kModeMoments).
 template <int Q, typename S>
-cudaError_t launch_step(const CUtensorMap& src, const StepArgs<typename Codec<S>::T, S>& a,
-                        dim3 grid, cudaStream_t stream, int mode);
+cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
+                        const StepArgs<typename Codec<S>::T, S>& a, dim3 grid,
+                        cudaStream_t stream, int mode);
 
 // CTAs of the step kernel that fit on one SM (occupancy query).
 template <int Q, typename S> int step_ctas_per_sm();
@@ -41,8 +47,8 @@ cudaError_t launch_decode(const S* buf, double* f, int nx, int ny, int64_t pitch
 template <int Q, typename T>
 cudaError_t launch_wall_prepare(const double* phi, const double* psr, const double* psa,
                                 const double* uw, double G_R, double G_A, double eps, int nx,
-                                int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint8_t* flags,
-                                int nchunk, cudaStream_t st);
+                                int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint32_t* flags,
+                                int nchunk_pad, cudaStream_t st);
 
 // Sum of rho_s candidates: sum_i f_i over all nodes of an FP64 [Q][N] array
 // (fsum) or of an [N] array (rho).  Deterministic two-pass Neumaier reduction.

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -67,6 +68,7 @@ template <typename T> struct Physics {
   T one_m_omega;     // 1 - 1 / tau
   T G;               // fluid-fluid coupling in F_FF = -G psi sum w psi r
   T rho0;            // exponential psi scale
+  T inv_rho0;        // 1 / rho0
   T eos_tv, eos_tu, eos_tl, eos_r1, eos_r2, eos_p1, eos_p2;
   T bfx, bfy;        // body-force density
   T rho_s;           // FP16S / BF16S shift
@@ -80,9 +82,9 @@ template <typename T> struct WallFields {
   const T* sy;
   const T* uwx;           // wall velocity (nullable)
   const T* uwy;
-  const uint8_t* flags;   // [ny][nchunk]: 1 if any wall term is non-zero in the 32-column chunk
-  int32_t nchunk;
-  int32_t active;         // 0: no wall at all
+  int32_t active;         // 0: no wall at all; else per-(row, 32-column chunk) flags
+                          // (uint32 [ny][nchunk_pad], non-zero where any wall term is
+                          // non-zero) arrive by TMA with each row
 };
 
 template <typename T> __device__ __forceinline__ T t_exp(T v);
@@ -97,7 +99,10 @@ template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqr
 template <int Q, typename T>
 __device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
   if (P.psi_kind == 0) {
-    return P.rho0 * (T(1) - t_exp<T>(-rho / P.rho0));
+    // FP64 divides like the oracle; FP32 multiplies by the reciprocal (exact
+    // for the usual rho0 = 1).
+    const T arg = sizeof(T) == 8 ? -rho / P.rho0 : -rho * P.inv_rho0;
+    return P.rho0 * (T(1) - t_exp<T>(arg));
   }
   constexpr T theta = T(Lattice<Q>::THETA);
   T p;
@@ -111,6 +116,21 @@ __device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
   return t_sqrt<T>(arg > T(0) ? arg : T(0));
 }
 
+// c * v for a lattice coefficient c known at compile time: 0, +-v or c v
+// (a product with zero is dropped; only the sign of a zero result can differ).
+template <int C, typename T> __device__ __forceinline__ T cmul(T v) {
+  if constexpr (C == 0) return T(0);
+  else if constexpr (C == 1) return v;
+  else if constexpr (C == -1) return -v;
+  else return T(C) * v;
+}
+// c_x u_x + c_y u_y with compile-time c.
+template <int CX, int CY, typename T> __device__ __forceinline__ T cdot(T ux, T uy) {
+  if constexpr (CX == 0) return cmul<CY>(uy);
+  else if constexpr (CY == 0) return cmul<CX>(ux);
+  else return cmul<CX>(ux) + cmul<CY>(uy);
+}
+
 // Exact reciprocal constants of the equilibrium for each lattice.
 template <int Q> struct EqConst;
 template <> struct EqConst<9> {
@@ -121,12 +141,27 @@ template <> struct EqConst<21> {
 };
 
 // f_i^eq = w_i rho [1 + c.u / theta + (c.u)^2 / (2 theta^2) - u^2 / (2 theta)]
+template <int Q, int I, typename T>
+__device__ __forceinline__ T feq_c(T rho, T ux, T uy, T usq_term) {
+  using L = Lattice<Q>;
+  using E = EqConst<Q>;
+  const T cu = cdot<L::cx(I), L::cy(I), T>(ux, uy);
+  return T(L::w(I)) * rho * (T(1) + cu * T(E::inv_theta) + cu * cu * T(E::inv_2theta2) - usq_term);
+}
 template <int Q, typename T>
 __device__ __forceinline__ T feq(int i, T rho, T ux, T uy, T usq_term) {
   using L = Lattice<Q>;
   using E = EqConst<Q>;
   const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
   return T(L::w(i)) * rho * (T(1) + cu * T(E::inv_theta) + cu * cu * T(E::inv_2theta2) - usq_term);
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1.
+template <int I, int N, typename F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
 }
 
 // Projection step (Sec. II, after Eq. f2): f_i <- w_i [rho + j.c_i / theta
@@ -152,6 +187,7 @@ __device__ __forceinline__ void project(T (&f)[Q], T rho, T jx, T jy) {
     f[i] = T(L::w(i)) * (rho + (jx * cx + jy * cy) * T(E::inv_theta) + contr * T(E::inv_2theta2));
   }
 }
+
 
 // a / b: FP64 divides (the oracle's rounding); FP32 multiplies by a reciprocal
 // computed once per node.
@@ -221,12 +257,12 @@ __device__ __forceinline__ void node_collide(const Physics<T>& P, T (&f)[Q], T r
   using L = Lattice<Q>;
   const T usq0 = (ux * ux + uy * uy) * T(E::inv_2theta);
   const T usq1 = (usx * usx + usy * usy) * T(E::inv_2theta);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const T e0 = feq<Q, T>(i, rho, ux, uy, usq0);
-    const T e1 = feq<Q, T>(i, rho, usx, usy, usq1);
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const T e0 = feq_c<Q, i, T>(rho, ux, uy, usq0);
+    const T e1 = feq_c<Q, i, T>(rho, usx, usy, usq1);
     f[i] = e1 + P.one_m_omega * (f[i] - e0);
-  }
+  });
   if constexpr (sizeof(T) == 4) {
     T moving = 0;
 #pragma unroll

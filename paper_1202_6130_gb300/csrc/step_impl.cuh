@@ -10,24 +10,27 @@ template <int Q, typename S, int MODE>
 static cudaError_t prepare_kernel() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
-  static cudaError_t once = cudaFuncSetAttribute(step_kernel<Q, S, Cfg::W, Cfg::NS, MODE>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Sh::SMEM);
+  static cudaError_t once = cudaFuncSetAttribute(
+      step_kernel<Q, S, Cfg::W, Cfg::NS, MODE, Cfg::MINB>,
+      cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   return once;
 }
 
 template <int Q, typename S>
-cudaError_t launch_step(const CUtensorMap& src, const StepArgs<typename Codec<S>::T, S>& a,
-                        dim3 grid, cudaStream_t stream, int mode) {
+cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
+                        const StepArgs<typename Codec<S>::T, S>& a, dim3 grid,
+                        cudaStream_t stream, int mode) {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   cudaError_t e;
   if (mode == kModeStep) {
     if ((e = prepare_kernel<Q, S, kModeStep>()) != cudaSuccess) return e;
-    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep><<<grid, Cfg::W, Sh::SMEM, stream>>>(src, a);
+    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>
+        <<<grid, Cfg::W, Sh::SMEM, stream>>>(src, flags, a);
   } else {
     if ((e = prepare_kernel<Q, S, kModeMoments>()) != cudaSuccess) return e;
-    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments><<<grid, Cfg::W, Sh::SMEM, stream>>>(src, a);
+    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments, Cfg::MINB>
+        <<<grid, Cfg::W, Sh::SMEM, stream>>>(src, flags, a);
   }
   return cudaGetLastError();
 }
@@ -38,15 +41,16 @@ template <int Q, typename S> int step_ctas_per_sm() {
   if (prepare_kernel<Q, S, kModeStep>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep>, Cfg::W, Sh::SMEM) != cudaSuccess)
+          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, Cfg::W, Sh::SMEM) !=
+      cudaSuccess)
     return 0;
   return n;
 }
 
 }  // namespace lbm
 
-#define LBM_INSTANTIATE_STEP(Q, S)                                                              \
-  template cudaError_t lbm::launch_step<Q, S>(const CUtensorMap&,                               \
-                                              const lbm::StepArgs<lbm::Codec<S>::T, S>&, dim3, \
-                                              cudaStream_t, int);                              \
+#define LBM_INSTANTIATE_STEP(Q, S)                                                         \
+  template cudaError_t lbm::launch_step<Q, S>(const CUtensorMap&, const CUtensorMap&,      \
+                                              const lbm::StepArgs<lbm::Codec<S>::T, S>&,   \
+                                              dim3, cudaStream_t, int);                    \
   template int lbm::step_ctas_per_sm<Q, S>();

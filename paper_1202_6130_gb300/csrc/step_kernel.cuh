@@ -16,12 +16,13 @@
 //
 // Schedule.  A CTA of W threads owns a strip of W columns and a segment of L
 // rows, and marches down the segment one node row at a time.  Each row's Q
-// source rows (one per population, shifted by -c_y) arrive by TMA into one of
-// NS shared-memory stages, NS - R - 1 rows ahead of use.  psi is computed once
-// per node (plus R halo nodes on each side of the strip) into a ring of 2R+1
-// rows; the collision of row k - R then reads its neighbours' psi from the
-// ring, so psi never touches HBM and the only redundant traffic is the 2R halo
-// columns and rows of each strip segment.
+// source rows (one per population, shifted by -c_y) and the row's wall flags
+// arrive by TMA in one of NS shared-memory stages, several rows ahead of use.
+// psi is computed once per node (plus R halo nodes on each side of the strip)
+// into a ring of 2R+2 rows; the collision of row k - R then reads its
+// neighbours' psi from the ring.  The extra ring row lets one barrier per row
+// order both the ring and the stage reuse.  psi never touches HBM; the only
+// redundant traffic is the 2R halo columns and rows of each strip segment.
 #pragma once
 
 #include <cuda.h>
@@ -56,24 +57,55 @@ template <typename T, typename S> struct StepArgs {
 
 template <int Q, typename S, int W, int NS> struct StepShape {
   using L = Lattice<Q>;
+  using P = Planes<Q>;
   using T = typename Codec<S>::T;
   static constexpr int R = L::R;
   static constexpr int GX = ghost_x<S, R>();
   static constexpr int GY = ghost_y<R>();
-  static constexpr int BW = W + 2 * GX;                                 // box width (elements)
-  static constexpr int SLOT = ((BW * (int)sizeof(S) + 127) / 128) * 128;  // bytes per box
-  static constexpr int SLOT_E = SLOT / (int)sizeof(S);
-  static constexpr int STAGE = Q * SLOT;
+  static constexpr int BW = W + 2 * GX;  // box width (elements)
+  // Planes are grouped by c_y; every group size of D2Q9 is 3 (one box of depth
+  // 3 per group), D2Q21 groups have 7, 3 and 1 planes (boxes of depth 1).
+  static constexpr int BD = (Q == 9) ? 3 : 1;
+  static constexpr int NBOX = Q / BD;
+  static constexpr int BOXSLOT = ((BD * BW * (int)sizeof(S) + 127) / 128) * 128;  // bytes
+  static constexpr int BOXSLOT_E = BOXSLOT / (int)sizeof(S);
+  static constexpr int CHUNKS = W / 32;  // wall-flag words per row
+  static constexpr int FLAG_SLOT = ((CHUNKS * 4 + 127) / 128) * 128;
+  static constexpr int STAGE = NBOX * BOXSLOT + FLAG_SLOT;
   static constexpr int RING_W = W + 2 * R;
-  static constexpr int RING_H = 2 * R + 1;
+  static constexpr int RING_H = 2 * R + 2;
   static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
                               RING_H * RING_W * (int)sizeof(T) + 16;
-  static constexpr uint32_t TX_BYTES = Q * BW * (uint32_t)sizeof(S);
+  static constexpr uint32_t TX_POP = Q * BW * (uint32_t)sizeof(S);
+  static constexpr uint32_t TX_FLAGS = CHUNKS * 4;
+  // Populations of the node row being collided stay in registers (R = 1) or
+  // are re-read from its stage (R > 1, where R rows of Q values would not fit).
+  static constexpr bool kRegs = (R == 1);
+  // Element offset of population i's pulled row inside a stage, and the c_y
+  // shared by the planes of box j: compile-time tables.
+  struct Tables {
+    int pop_row[Q];
+    int box_cy[NBOX];
+  };
+  static constexpr Tables make_tables() {
+    Tables t{};
+    for (int i = 0; i < Q; ++i) {
+      const int p = P::kTable.plane[i];
+      t.pop_row[i] = (p / BD) * BOXSLOT_E + (p % BD) * BW;
+      if (p % BD == 0) t.box_cy[p / BD] = L::cy(i);
+    }
+    return t;
+  }
+  static constexpr Tables kTab = make_tables();
+  static_assert(W % 32 == 0 && W >= 64 && CHUNKS <= 256, "strip width");
+  static_assert(NS >= R + 2, "pipeline depth");
+  static_assert(Q % BD == 0, "box depth");
 };
 
-template <int Q, typename S, int W, int NS, int MODE>
-__global__ void __launch_bounds__(W)
-    step_kernel(const __grid_constant__ CUtensorMap src, const StepArgs<typename Codec<S>::T, S> a) {
+template <int Q, typename S, int W, int NS, int MODE, int MINB>
+__global__ void __launch_bounds__(W, MINB)
+    step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
+                const StepArgs<typename Codec<S>::T, S> a) {
   using Sh = StepShape<Q, S, W, NS>;
   using L = Lattice<Q>;
   using T = typename Codec<S>::T;
@@ -91,15 +123,22 @@ __global__ void __launch_bounds__(W)
   int* s_abort = reinterpret_cast<int*>(ring + Sh::RING_H * Sh::RING_W);
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const int x0 = blockIdx.x * W;
   const int y0 = blockIdx.y * a.tile_rows;
   const int Lr = min(a.tile_rows, a.ny - y0);
   const int K = Lr + 2 * R;  // node rows y0 - R .. y0 + Lr + R - 1
   const int x = x0 + tid;
+  const bool wall_on = a.wall.active != 0;
+  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
 
+  // Roles: the first lane of the last warp issues the TMA copies; the first
+  // lanes of warps 0 and 1 form the left and right halo psi.
+  constexpr int kIssuer = W - 32;
   uint64_t policy = 0;
-  if (tid == 0) {
+  if (tid == kIssuer) {
     prefetch_tensormap(&src);
+    if (wall_on) prefetch_tensormap(&flg);
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     *s_abort = 0;
@@ -108,63 +147,109 @@ __global__ void __launch_bounds__(W)
   }
   __syncthreads();
 
-  // Thread 0 issues the Q boxes of node row k into stage k % NS.
+  // The issuer copies node row k into stage k % NS: one box per plane group
+  // (the group's source row is y - c_y) plus, with walls, the row's flag words.
   auto issue = [&](int k) {
     const int s = k % NS;
     const int ynode = y0 - R + k;
-    mbar_arrive_expect_tx(&bars[s], Sh::TX_BYTES);
+    mbar_arrive_expect_tx(&bars[s], tx_bytes);
     unsigned char* st = stages + s * Sh::STAGE;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      tma_load_3d(st + i * Sh::SLOT, &src, &bars[s], x0, ynode - L::cy(i) + GY, i, policy);
-    }
+    static_for<0, Sh::NBOX>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      constexpr int cy = Sh::kTab.box_cy[j];
+      tma_load_3d(st + j * Sh::BOXSLOT, &src, &bars[s], x0, ynode - cy + GY, j * Sh::BD, policy);
+    });
+    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, &flg, &bars[s], x0 >> 5, ynode);
   };
   int issued = 0;
-  if (tid == 0) {
+  if (tid == kIssuer) {
     const int n0 = min(NS, K);
 #pragma unroll 1
     for (int k = 0; k < n0; ++k) issue(k);
     issued = n0;
   }
 
-  // Per-population decode shift w_i rho_s (zero unless shifted storage).
   const T rho_s = a.phys.rho_s;
-
-  auto load_pop = [&](const S* st, int i, int xl) -> T {
-    // xl: node column relative to x0; pulled from column xl - c_x in the box,
-    // whose first element is node column -GX.
-    return C::dec(st[i * Sh::SLOT_E + xl + GX - L::cx(i)], T(L::w(i)) * rho_s);
+  // Population I of node column xl (relative to x0) from a stage: pulled from
+  // column xl - c_x of its box row, whose first element is node column -GX.
+  auto load_pop = [&](const S* st, auto ic, int xl) -> T {
+    constexpr int i = decltype(ic)::value;
+    constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
+    return C::dec(st[off + xl], T(L::w(i)) * rho_s);
   };
-
   auto psi_at = [&](const S* st, int xl) -> T {
-    T rho = load_pop(st, 0, xl);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) rho += load_pop(st, i, xl);
+    T rho = 0;
+    static_for<0, Q>([&](auto ic) {
+      const T v = load_pop(st, ic, xl);
+      rho = (decltype(ic)::value == 0) ? v : rho + v;
+    });
     return pseudo_potential<Q, T>(a.phys, rho);
   };
+  auto flags_of = [&](const unsigned char* st) -> uint32_t {
+    return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::NBOX * Sh::BOXSLOT)[warp] : 0u;
+  };
 
+  T fnext[Q];            // kRegs: populations of the row whose psi was just formed
+  uint32_t flag_next = 0;
   int k = 0;
 #pragma unroll 1
   for (; k < K; ++k) {
     const int s = k % NS;
     if (!mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u)) *s_abort = 1;
-    const S* st = reinterpret_cast<const S*>(stages + s * Sh::STAGE);
+    const unsigned char* stb = stages + s * Sh::STAGE;
+    const S* st = reinterpret_cast<const S*>(stb);
+
+    // Populations of the row collided in this iteration (row k - R).
+    T f[Q];
+    uint32_t flag;
+    if constexpr (Sh::kRegs) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = fnext[i];
+      flag = flag_next;
+    }
+
+    // psi of node row k: own column and the halo columns.
     T* ring_row = ring + (k % Sh::RING_H) * Sh::RING_W;
-    ring_row[tid + R] = psi_at(st, tid);
-    if (tid < 2 * R) {
-      const int xl = tid < R ? tid - R : W + tid - R;
-      ring_row[xl + R] = psi_at(st, xl);
+    {
+      T rho = 0;
+      static_for<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const T v = load_pop(st, ic, tid);
+        if constexpr (Sh::kRegs) fnext[i] = v;
+        rho = (i == 0) ? v : rho + v;
+      });
+      ring_row[tid + R] = pseudo_potential<Q, T>(a.phys, rho);
+      if constexpr (Sh::kRegs) flag_next = flags_of(stb);
+    }
+    {
+      const int lane = tid & 31;
+      if (warp < 2 && lane < R) {
+        const int xl = warp == 0 ? lane - R : W + lane;
+        ring_row[xl + R] = psi_at(st, xl);
+      }
     }
     __syncthreads();
     if (*s_abort) break;
 
+    // Every thread has finished iteration k - 1: recycle the stage it last used.
+    if (tid == kIssuer) {
+      const int fr = k - 1 - (Sh::kRegs ? 0 : R);
+      if (fr >= 0 && fr + NS < K) {
+        issue(fr + NS);
+        issued = fr + NS + 1;
+      }
+    }
+
     if (k >= 2 * R) {
       const int ko = k - R;
       const int yo = y0 - R + ko;
-      const S* sto = reinterpret_cast<const S*>(stages + (ko % NS) * Sh::STAGE);
-      T f[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = load_pop(sto, i, tid);
+      if constexpr (!Sh::kRegs) {
+        const unsigned char* sto = stages + (ko % NS) * Sh::STAGE;
+        static_for<0, Q>([&](auto ic) {
+          f[decltype(ic)::value] = load_pop(reinterpret_cast<const S*>(sto), ic, tid);
+        });
+        flag = flags_of(sto);
+      }
       T rho, jx, jy;
       node_moments<Q, T>(f, rho, jx, jy);
       const T inv_rho = T(1) / rho;
@@ -174,29 +259,27 @@ __global__ void __launch_bounds__(W)
       // sum_i w_i psi(x + c_i) c_i from the ring (rest state contributes 0).
       const T psi_c = ring[(ko % Sh::RING_H) * Sh::RING_W + tid + R];
       T sfx = 0, sfy = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::cx(i) == 0 && L::cy(i) == 0) continue;
-        const T nb = ring[((ko + L::cy(i)) % Sh::RING_H) * Sh::RING_W + tid + R + L::cx(i)];
-        const T wn = T(L::w(i)) * nb;
-        if (L::cx(i) != 0) sfx += wn * T(L::cx(i));
-        if (L::cy(i) != 0) sfy += wn * T(L::cy(i));
-      }
+      static_for<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if constexpr (L::cx(i) != 0 || L::cy(i) != 0) {
+          const T nb = ring[((ko + L::cy(i)) % Sh::RING_H) * Sh::RING_W + tid + R + L::cx(i)];
+          const T wn = T(L::w(i)) * nb;
+          if constexpr (L::cx(i) != 0) sfx += cmul<L::cx(i)>(wn);
+          if constexpr (L::cy(i) != 0) sfy += cmul<L::cy(i)>(wn);
+        }
+      });
 
-      // Wall terms: only where the per-(row, 32-column chunk) flag is set.
-      bool has_wall = false;
+      // Wall terms only on flagged (row, 32-column chunk) pairs.
+      const bool has_wall = flag != 0u && x < a.nx;
       T phie = 0, Sx = 0, Sy = 0, uwx = 0, uwy = 0;
-      if (a.wall.active && x < a.nx) {
-        has_wall = a.wall.flags[(int64_t)yo * a.wall.nchunk + (x >> 5)] != 0;
-        if (has_wall) {
-          const int64_t n = (int64_t)yo * a.nx + x;
-          phie = a.wall.phie[n];
-          Sx = a.wall.sx[n];
-          Sy = a.wall.sy[n];
-          if (a.wall.uwx) {
-            uwx = a.wall.uwx[n];
-            uwy = a.wall.uwy[n];
-          }
+      if (has_wall) {
+        const int64_t n = (int64_t)yo * a.nx + x;
+        phie = a.wall.phie[n];
+        Sx = a.wall.sx[n];
+        Sy = a.wall.sy[n];
+        if (a.wall.uwx) {
+          uwx = a.wall.uwx[n];
+          uwy = a.wall.uwy[n];
         }
       }
       T Fx, Fy;
@@ -211,11 +294,11 @@ __global__ void __launch_bounds__(W)
           if (a.phys.project) project<Q, T>(f, rho, jx, jy);
           node_collide<Q, T>(a.phys, f, rho, ux, uy, usx, usy);
           // Primary store plus periodic images inside the ghost frame.
-          S* out = a.fout;
-          const int64_t row = (int64_t)(yo + GY) * a.pitch;
-#pragma unroll
-          for (int i = 0; i < Q; ++i)
-            out[i * a.plane + row + x + GX] = C::enc(f[i], T(L::w(i)) * rho_s);
+          S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
+          static_for<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            out[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i], T(L::w(i)) * rho_s);
+          });
           const bool edge = x < GX || x >= a.nx - GX || yo < GY || yo >= a.ny - GY;
           if (edge) {
             int xa = x;
@@ -225,10 +308,11 @@ __global__ void __launch_bounds__(W)
             for (int ym = ya; ym < a.ny + GY; ym += a.ny) {
               for (int xm = xa; xm < a.nx + GX; xm += a.nx) {
                 if (xm == x && ym == yo) continue;
-                const int64_t off = (int64_t)(ym + GY) * a.pitch + xm + GX;
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                  out[i * a.plane + off] = C::enc(f[i], T(L::w(i)) * rho_s);
+                S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
+                static_for<0, Q>([&](auto ic) {
+                  constexpr int i = decltype(ic)::value;
+                  o2[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i], T(L::w(i)) * rho_s);
+                });
               }
             }
           }
@@ -247,20 +331,12 @@ __global__ void __launch_bounds__(W)
         }
       }
     }
-    __syncthreads();
-    if (tid == 0 && k >= R) {
-      const int kk = k - R + NS;
-      if (kk < K) {
-        issue(kk);
-        issued = kk + 1;
-      }
-    }
   }
 
   if (*s_abort) {
     // A stage never completed.  Record it, then give the copies still in
     // flight a bounded chance to land before the CTA's shared memory goes away.
-    if (tid == 0) {
+    if (tid == kIssuer) {
       atomicOr(a.status, kStatusTimeout);
       for (int r = k; r < issued; ++r) mbar_wait_bounded(&bars[r % NS], (uint32_t)(r / NS) & 1u);
     }

@@ -1,0 +1,45 @@
+"""The host-side measurements recover known answers from synthetic fields."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1202_6130_gb300 import analysis as A
+import workloads as W
+
+
+@pytest.mark.parametrize("theta_deg", [40.0, 90.0, 120.0])
+def test_contact_angle_of_an_exact_circular_cap(theta_deg):
+    nx, ny = 400, 240
+    dist = W.wall_distance_slab(nx, ny)
+    phi, _, _ = W.wall_core_tail(dist, 3.0)
+    yb = A.surface_line(phi[:, 0], 0.5)
+    R = 60.0
+    yc = yb - R * math.cos(math.radians(theta_deg))
+    rho = W.droplet_density(nx, ny, [(200.0, yc)], [R], 2.0, 0.1, 2.0)
+    ca = A.contact_angle(rho, phi, 2.0, 0.1)
+    assert abs(ca.theta_deg - theta_deg) < 0.5, ca
+    assert abs(ca.R - R) < 0.5
+
+
+def test_slip_length_of_a_shifted_parabola():
+    ny, nx = 120, 4
+    dist = W.wall_distance_slab(nx, ny)
+    phi, _, _ = W.wall_core_tail(dist, 3.0)
+    yw = A.surface_line(phi[:, 0], 0.01)
+    b_true = 2.5
+    # u = A (y - y0)(y1 - y), zero at y_w - b and ny - y_w + b
+    y0, y1 = yw - b_true, ny - yw + b_true
+    y = np.arange(ny, dtype=float)[:, None]
+    u = 1e-4 * (y - y0) * (y1 - y) * np.ones((1, nx))
+    s = A.slip_length(u, phi)
+    # Navier slip: u(y_w) / u'(y_w) of the exact parabola
+    uw = 1e-4 * (yw - y0) * (y1 - yw)
+    du = 1e-4 * ((y1 - yw) - (yw - y0))
+    assert abs(s.slip_length - uw / du) < 1e-8
+    assert abs(s.curvature + 2e-4) < 1e-12
+
+
+def test_laplace_pressure_of_a_flat_state_is_zero():
+    rho = np.full((64, 64), 1.3)
+    assert abs(A.laplace_jump(rho, -5.5, (32, 32), 5, 20)) < 1e-15

@@ -60,12 +60,22 @@ def droplet_density(nx: int, ny: int, centers, radii, rho_l: float, rho_v: float
     rho = rho_v + (rho_l - rho_v) * 0.5 * (1 - tanh(2 (r - R) / width)), with r
     the plain Euclidean distance to the centre (the disc is not wrapped).
     """
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     rho = np.full((ny, nx), rho_v, dtype=np.float64)
+    # Each cap is evaluated inside its bounding box grown by 12 widths: farther
+    # out (rho_l - rho_v)(1 - tanh)/2 < 2e-21, which cannot change rho_v in FP64,
+    # so the result is identical to evaluating every cap everywhere.
+    margin = 12.0 * width + 1.0
     for (cx, cy), R in zip(centers, radii):
+        x0 = max(0, int(math.floor(cx - R - margin)))
+        x1 = min(nx, int(math.ceil(cx + R + margin)) + 1)
+        y0 = max(0, int(math.floor(cy - R - margin)))
+        y1 = min(ny, int(math.ceil(cy + R + margin)) + 1)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        y, x = np.mgrid[y0:y1, x0:x1].astype(np.float64)
         r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
         cap = rho_v + (rho_l - rho_v) * 0.5 * (1.0 - np.tanh(2.0 * (r - R) / width))
-        rho = np.maximum(rho, cap)
+        rho[y0:y1, x0:x1] = np.maximum(rho[y0:y1, x0:x1], cap)
     return rho
 
 
