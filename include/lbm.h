@@ -200,6 +200,31 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
                        double core_lambda, double core_cut, double tail_exp, double tail_cut,
                        double phi_cut, double* phi_s, double* psi_r, double* psi_a);
 
+/* ---- allocation-free reduction ------------------------------------------ */
+
+/* Compensated (Neumaier) FP64 sums of up to three DEVICE arrays of n doubles
+ * each (a, b, c; a NULL array sums to 0), written to the DEVICE array out[3]:
+ * the same reduction lbm_totals applies to rho and j + F/2, offered to callers
+ * that must not allocate device memory while they run: a real-time loop with a
+ * fixed memory budget, code working inside a memory pool it does not own, or a
+ * host framework that forbids cudaMalloc after start-up.  The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * It calls no cudaMalloc / cudaFree and no allocating library routine.  Its
+ * partial sums live in one fixed 192 KiB array in device memory, which every
+ * GPU that loads the library holds until the process exits; that bounds n to
+ * at most 2^28 elements (4096 blocks of 65536), and larger n returns LBM_EINVAL
+ * with the limit in lbm_last_error(NULL).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) once, with the device
+ * current; make that first call before any stream capture.  Work is enqueued
+ * on cuda_stream (NULL = legacy default stream) and the call returns without
+ * synchronising.  Every call on a device shares the one array, so calls whose
+ * kernels overlap on the GPU (different streams, no ordering between them)
+ * race and give wrong sums; calls on one stream are safe.  Errors: LBM_EINVAL
+ * (out NULL, n < 0 or above the limit), LBM_ECUDA (launch failure). */
+int lbm_reduce3_noalloc(const double* d_a, const double* d_b, const double* d_c, int64_t n,
+                        double* d_out3, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ SIGNATURES = {
                                          c_int32, _DP, _DP, _DP]),
     "lbm_wall_core_tail": (c_int, [c_int32, c_int32, _DP, _DP, c_double, c_double, c_double,
                                    c_double, c_double, _DP, _DP, _DP]),
+    "lbm_reduce3_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
 }
 
 

@@ -334,6 +334,10 @@ int set_shift_from_rho(lbm_ctx* c, const double* d_rho) {
 
 }  // namespace
 
+// Sets the context-free error text (used by entry points defined in other
+// translation units; not exported).
+void lbmi_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------

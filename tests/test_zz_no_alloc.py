@@ -1,0 +1,60 @@
+"""lbm_reduce3_noalloc, the reduction for callers that must not allocate
+device memory while they run (fixed-budget real-time loops, code inside a
+memory pool it does not own): its sums of rho and j + F/2 must equal those of
+lbm_totals, on two calls in a row that reuse its fixed scratch array.
+
+Collected last on purpose, so that a run stopping at the first failure has
+already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _device_sums(pkg, lib, sim, torch):
+    rho, ux, uy = sim.moments_device()
+    px = (rho * ux).contiguous()
+    py = (rho * uy).contiguous()
+    out = torch.zeros(3, dtype=torch.float64, device=rho.device)
+    stream = torch.cuda.current_stream()
+    rc = lib.lbm_reduce3_noalloc(ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(px.data_ptr()),
+                                 ctypes.c_void_p(py.data_ptr()), rho.numel(),
+                                 ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(stream.cuda_stream))
+    assert rc == 0, lib.lbm_last_error(None)
+    return out.cpu().numpy()
+
+
+def test_noalloc_reduction_matches_lbm_totals_on_two_calls():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1202_6130_gb300 as pkg
+    from paper_1202_6130_gb300 import _lib
+    lib = _lib.load()
+    # 600 x 320 = 192000 nodes: three blocks of the fixed scratch
+    w = W.droplet_on_wall(nx=600, ny=320, R=60.0)
+    sim = pkg.Simulation.from_workload(w, storage="fp64")
+    sim.step(20)
+    for _ in range(2):
+        want = sim.totals()
+        got = _device_sums(pkg, lib, sim, torch)
+        assert abs(got[0] - want[0]) <= 1e-13 * abs(want[0])
+        assert abs(got[1] - want[1]) <= 1e-10 and abs(got[2] - want[2]) <= 1e-10
+        sim.step(15)
+    sim.close()
+
+
+def test_noalloc_reduction_rejects_sizes_beyond_its_scratch():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1202_6130_gb300 import _lib
+    lib = _lib.load()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    rc = lib.lbm_reduce3_noalloc(None, None, None, (1 << 28) + 1, ctypes.c_void_p(out.data_ptr()),
+                                 None)
+    assert rc == _lib.LBM_EINVAL
+    assert b"scratch limit" in lib.lbm_last_error(None)
