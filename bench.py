@@ -28,6 +28,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -235,8 +237,50 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: int = 256):
+    """The batched parameter sweep: n independent lattices, sizes log-uniform in
+    64x32 .. 1024x512 (seed 2), each with its own tau, G, G_R, G_A and a drop or
+    a sheared film.  Times `steps` steps run one lattice after another (one
+    launch per lattice per step) against the same steps of all lattices in one
+    batch (one fused launch per step, two-step CUDA graph, autotuned tiles)."""
+    ws = W.batch_sweep(n=n, seed=2)
+    nodes = sum(w.nx * w.ny for w in ws)
+    sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
+    for sm in sims:
+        sm.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sm in sims:
+        sm.step(steps)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    b = pkg.Batch()
+    for sm in sims:
+        b.add(sm)
+    tune = b.autotune(steps_per_trial=10)
+    b.step(4)
+    b.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(b.stream)
+    b.step(steps)
+    ev1.record(b.stream)
+    b.synchronize()
+    t_bat = time.perf_counter() - t0
+    t_bat_dev = ev0.elapsed_time(ev1) / 1e3
+    finite = all(bool(np.isfinite(sm.moments()[0]).all()) for sm in sims[:8])
+    b.close()
+    for sm in sims:
+        sm.close()
+    return {"lattices": n, "nodes": nodes, "steps": steps, "storage": storage,
+            "sequential_mlups": nodes * steps / t_seq / 1e6,
+            "batched_mlups": nodes * steps / t_bat / 1e6,
+            "batched_device_mlups": nodes * steps / t_bat_dev / 1e6,
+            "speedup": t_seq / t_bat, "tiling": tune, "finite": finite,
+            "gpu_launches_batched": steps}
+
+
 def run_gpu(args, world, rank, local):
-    import numpy as np
     import torch
     torch.cuda.set_device(local)
     import paper_1202_6130_gb300 as pkg
@@ -321,6 +365,8 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_batch:
+        line["batch"] = measure_batch(pkg, torch, W)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -335,6 +381,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--storage", default="fp32", choices=list(DTYPE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched parameter-sweep measurement")
     ap.add_argument("--size", default=f"{NX}x{NY}",
                     help="lattice size NXxNY (the same recipe at another size, for profiling)")
     args = ap.parse_args(argv)

@@ -200,6 +200,43 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
                        double core_lambda, double core_cut, double tail_exp, double tail_cut,
                        double phi_cut, double* phi_s, double* psi_r, double* psi_a);
 
+/* ---- batches: many lattices advanced by one launch per step ---------------- */
+
+/* A batch advances several contexts (its members) together: every time step of
+ * every member is one launch of one fused kernel, whose CTAs march a list of
+ * (member, strip, segment) tiles; two consecutive steps are captured once in a
+ * CUDA graph and replayed.  Members must share lattice and storage but may
+ * differ in size and in every physical parameter.  Members stay owned by the
+ * caller (destroy a member only after removing it), keep their own device
+ * memory, and can still be read with lbm_moments and friends between batch
+ * steps.  Stepping a member on its own, or changing its wall or stream,
+ * between batch steps is allowed; the batch notices and rebuilds its tile
+ * list.  The batch's own small descriptor arrays come from a (nullable)
+ * allocator.  Graph capture needs a non-default stream; with a NULL stream
+ * every step is a plain launch.  lbm_batch_step orders itself with the
+ * members' own streams by events: it starts after work already enqueued on
+ * them, and work enqueued on them afterwards waits for it.  Errors are
+ * reported by lbm_batch_last_error. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(const lbm_allocator* a, void* cuda_stream, lbm_batch** out);
+/* Adds c (populations set; same lattice and storage as the other members). */
+int lbm_batch_add(lbm_batch* b, lbm_ctx* c);
+int lbm_batch_remove(lbm_batch* b, lbm_ctx* c);
+int lbm_batch_size(const lbm_batch* b, int32_t* n);
+/* Tile shape: tile_rows rows per segment (0: each member's own choice) and
+ * ctas persistent CTAs that deal the tiles round-robin (0: one CTA per tile). */
+int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas);
+/* Advances every member by nsteps time steps; enqueued on the batch stream. */
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+/* Times each candidate tiling (rows 4..64 x {one CTA per tile, one persistent
+ * wave}) for steps_per_trial steps (plus 2 warm-up steps) on the members
+ * themselves -- so they advance by those steps -- and keeps the fastest.
+ * Outputs may be NULL.  Synchronises the stream. */
+int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile_rows,
+                       int32_t* best_ctas, double* best_ms_per_step);
+int lbm_batch_destroy(lbm_batch* b); /* NULL ok; members are untouched */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* ---- allocation-free reduction ------------------------------------------ */
 
 /* Compensated (Neumaier) FP64 sums of up to three DEVICE arrays of n doubles

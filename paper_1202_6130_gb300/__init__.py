@@ -8,8 +8,8 @@ hand-written sm_103a CUDA kernel behind the C ABI of ``include/lbm.h``;
 """
 from ._lib import (LBM_BF16S, LBM_D2Q9, LBM_D2Q21, LBM_FP16S, LBM_FP32, LBM_FP64, LBM_PSI_EOS,
                    LBM_PSI_EXP, LbmError, load)
-from .sim import Simulation, wall_core_tail, wall_gaussian_filter
+from .sim import Batch, Simulation, wall_core_tail, wall_gaussian_filter
 
-__all__ = ["Simulation", "LbmError", "load", "wall_gaussian_filter", "wall_core_tail",
+__all__ = ["Simulation", "Batch", "LbmError", "load", "wall_gaussian_filter", "wall_core_tail",
            "LBM_D2Q9", "LBM_D2Q21", "LBM_FP64", "LBM_FP32", "LBM_FP16S", "LBM_BF16S",
            "LBM_PSI_EXP", "LBM_PSI_EOS"]

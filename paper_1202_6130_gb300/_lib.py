@@ -77,6 +77,16 @@ SIGNATURES = {
     "lbm_wall_core_tail": (c_int, [c_int32, c_int32, _DP, _DP, c_double, c_double, c_double,
                                    c_double, c_double, _DP, _DP, _DP]),
     "lbm_reduce3_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "lbm_batch_create": (c_int, [POINTER(lbm_allocator), c_void_p, POINTER(c_void_p)]),
+    "lbm_batch_add": (c_int, [c_void_p, c_void_p]),
+    "lbm_batch_remove": (c_int, [c_void_p, c_void_p]),
+    "lbm_batch_size": (c_int, [c_void_p, POINTER(c_int32)]),
+    "lbm_batch_set_tiling": (c_int, [c_void_p, c_int32, c_int32]),
+    "lbm_batch_step": (c_int, [c_void_p, c_int64]),
+    "lbm_batch_autotune": (c_int, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
+                                   POINTER(c_double)]),
+    "lbm_batch_destroy": (c_int, [c_void_p]),
+    "lbm_batch_last_error": (c_char_p, [c_void_p]),
 }
 
 
@@ -110,6 +120,12 @@ def load() -> ctypes.CDLL:
 def check(rc: int, ctx=None):
     if rc != LBM_OK:
         msg = load().lbm_last_error(ctx)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+def check_batch(rc: int, batch=None):
+    if rc != LBM_OK:
+        msg = load().lbm_batch_last_error(batch)
         raise LbmError(rc, msg.decode() if msg else "")
 
 

@@ -51,6 +51,7 @@ struct lbm_ctx {
   int64_t steps = 0;
   double rho_s = 0.0;
   int tile_rows = 0, grid_x = 0, grid_y = 0;
+  uint64_t version = 0;  // bumped whenever device pointers or parameters change
 };
 
 namespace {
@@ -178,29 +179,18 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
   return LBM_OK;
 }
 
-// Rows per CTA: the grid (strips x segments) should fill whole waves of
-// resident CTAs while keeping the 2R halo rows per segment a small fraction.
-int choose_tile_rows(int nx, int ny, int W, int R, int ctas_per_sm, int num_sms) {
+// Rows per CTA segment.  Measured on GB300 (8192x4096 D2Q9): short segments
+// win although their 2R halo rows are re-read (from L2), because many waves of
+// short CTAs keep the concurrently active tiles in a compact band of rows and
+// balance the SMs dynamically; FP32 is fastest near 8 rows, 16-bit storage
+// near 24-48.  Small lattices get shorter segments so that the grid still
+// covers at least two waves of resident CTAs.
+int choose_tile_rows(int nx, int ny, int W, int esize, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  double best = -1.0;
-  int best_L = ny;
-  for (int L = 1; L <= ny; ++L) {
-    const int gy = (ny + L - 1) / L;
-    if (L > 1 && (ny + L - 2) / (L - 1) == gy) continue;  // same grid as a smaller L
-    const int64_t ctas = (int64_t)gx * gy;
-    const int64_t waves = (ctas + slots - 1) / slots;
-    const double fill = (double)ctas / (double)(waves * slots);
-    const double halo = (double)L / (double)(L + 2 * R);
-    // mild preference for fewer, longer segments (pipeline start-up per CTA)
-    const double startup = (double)L / (double)(L + 8);
-    const double score = fill * halo * startup;
-    if (score > best + 1e-12) {
-      best = score;
-      best_L = L;
-    }
-  }
-  return best_L;
+  int L = esize == 2 ? 32 : (esize == 4 ? 8 : 32);
+  while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
+  return std::max(1, std::min(L, ny));
 }
 
 template <int Q, typename S> int setup_layout(lbm_ctx* c) {
@@ -232,7 +222,7 @@ template <int Q, typename S> int setup_layout(lbm_ctx* c) {
     return fail(c, LBM_ECUDA, "step kernel cannot be resident (%s)", cudaGetErrorString(e));
   }
   c->tile_rows = c->p.tile_rows > 0 ? std::min(c->p.tile_rows, c->p.ny)
-                                    : choose_tile_rows(c->p.nx, c->p.ny, c->W, c->R, cps, sms);
+                                    : choose_tile_rows(c->p.nx, c->p.ny, c->W, c->esize, cps, sms);
   c->grid_x = (c->p.nx + c->W - 1) / c->W;
   c->grid_y = (c->p.ny + c->tile_rows - 1) / c->tile_rows;
   return LBM_OK;
@@ -263,9 +253,10 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   return P;
 }
 
+// Step arguments for a pass that reads the current buffer of c.
 template <int Q, typename S>
-int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, int momentum,
-             S* fout) {
+StepArgs<typename Codec<S>::T, S> make_args(const lbm_ctx* c, S* fout, double* o_rho,
+                                            double* o_ux, double* o_uy, int momentum) {
   using T = typename Codec<S>::T;
   StepArgs<T, S> a{};
   a.phys = make_physics<T>(c);
@@ -286,6 +277,13 @@ int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, in
   a.out_uy = o_uy;
   a.momentum = momentum;
   a.status = c->d_status;
+  return a;
+}
+
+template <int Q, typename S>
+int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, int momentum,
+             S* fout) {
+  const auto a = make_args<Q, S>(c, fout, o_rho, o_ux, o_uy, momentum);
   // Without walls the flag map is never read; the population map stands in.
   const CUtensorMap& fm = c->has_wall ? c->flag_map : c->tmap[c->cur];
   CK(c, launch_step<Q, S>(c->tmap[c->cur], fm, a, dim3(c->grid_x, c->grid_y), c->stream, mode));
@@ -401,6 +399,7 @@ int lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
   int rc = guard(c);
   if (rc) return rc;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->version += 1;
   return LBM_OK;
 }
 
@@ -473,6 +472,7 @@ int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const dou
     c->wall_uwx = c->wall_uwy = nullptr;
   }
   c->has_wall = phi_s || psi_r || psi_a;
+  c->version += 1;
   CK(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -746,4 +746,394 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: many lattices of one (lattice, storage) kind advanced together
+// ---------------------------------------------------------------------------
 }  // extern "C"
+
+struct lbm_batch {
+  lbm_allocator alloc{};
+  bool user_alloc = false;
+  cudaStream_t stream = nullptr;
+  std::vector<lbm_ctx*> members;
+  std::vector<uint64_t> versions;
+  std::vector<int> cur0;  // member cur at build time
+  int Q = 0, storage = -1;
+  int tile_rows = 0;  // 0: each member's own choice
+  int ctas = 0;       // 0: one CTA per tile; > 0: that many persistent CTAs
+  bool dirty = true;
+  void* d_members = nullptr;
+  size_t cap_members = 0;
+  void* d_tiles = nullptr;
+  size_t cap_tiles = 0;
+  void* d_first = nullptr;
+  size_t cap_first = 0;
+  int ntiles = 0, nctas = 0;
+  int64_t phase = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t order_ev = nullptr;  // orders member streams with the batch stream
+  std::string err;
+  bool poisoned = false;
+};
+
+namespace {
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (b) {
+    b->err = msg;
+    if (code == LBM_ECUDA) b->poisoned = true;
+  } else {
+    g_err = msg;
+  }
+  return code;
+}
+
+#define BCK(b, ...)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (__VA_ARGS__);                                                    \
+    if (e_ != cudaSuccess)                                                             \
+      return bfail((b), LBM_ECUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+  } while (0)
+
+void* balloc(lbm_batch* b, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (b->user_alloc)
+    p = b->alloc.alloc(bytes, b->alloc.user);
+  else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void bfree(lbm_batch* b, void* p) {
+  if (!p) return;
+  if (b->user_alloc)
+    b->alloc.free(p, b->alloc.user);
+  else
+    cudaFree(p);
+}
+
+int bgrow(lbm_batch* b, void** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return LBM_OK;
+  if (*p) {
+    cudaStreamSynchronize(b->stream);
+    bfree(b, *p);
+  }
+  *p = balloc(b, need);
+  *cap = *p ? need : 0;
+  return *p ? LBM_OK : bfail(b, LBM_ENOMEM, "batch descriptor of %zu bytes", need);
+}
+
+void drop_graph(lbm_batch* b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+}
+
+template <int Q, typename S> int batch_build(lbm_batch* b) {
+  using T = typename Codec<S>::T;
+  using M = BatchMember<T, S>;
+  constexpr int W = StepConfig<Q, S>::W;
+  const int n = (int)b->members.size();
+  std::vector<M> hm(n);
+  std::vector<BatchTile> tiles;
+  b->versions.assign(n, 0);
+  b->cur0.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    lbm_ctx* c = b->members[i];
+    M& m = hm[i];
+    std::memset(&m, 0, sizeof m);
+    m.map[0] = c->tmap[0];
+    m.map[1] = c->tmap[1];
+    m.flags = c->has_wall ? c->flag_map : c->tmap[0];
+    for (int d = 0; d < 2; ++d)
+      m.args[d] = make_args<Q, S>(c, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
+    m.cur = c->cur;
+    b->versions[i] = c->version;
+    b->cur0[i] = c->cur;
+  }
+  // Tiles in row-band-major order: all strips of a segment before the next.
+  for (int i = 0; i < n; ++i) {
+    const lbm_ctx* c = b->members[i];
+    const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
+    for (int y0 = 0; y0 < c->p.ny; y0 += L)
+      for (int x0 = 0; x0 < c->p.nx; x0 += W)
+        tiles.push_back({i, x0, y0, std::min(L, c->p.ny - y0)});
+  }
+  std::vector<int32_t> first;
+  std::vector<BatchTile> order;
+  if (b->ctas <= 0) {
+    b->nctas = (int)tiles.size();
+    order = tiles;
+    first.resize(tiles.size() + 1);
+    for (size_t t = 0; t <= tiles.size(); ++t) first[t] = (int32_t)t;
+  } else {
+    // Persistent CTAs, tiles dealt round-robin: CTA k gets tiles k, k + G, ...
+    b->nctas = std::min<int>(b->ctas, (int)tiles.size());
+    const int G = b->nctas;
+    first.assign(G + 1, 0);
+    for (int k = 0; k < G; ++k) {
+      first[k] = (int32_t)order.size();
+      for (size_t t = k; t < tiles.size(); t += G) order.push_back(tiles[t]);
+    }
+    first[G] = (int32_t)order.size();
+  }
+  b->ntiles = (int)order.size();
+  batch_ctas_per_sm<Q, S>();  // sets the kernel's shared-memory attribute outside any capture
+  int rc = bgrow(b, &b->d_members, &b->cap_members, sizeof(M) * std::max(1, n));
+  if (!rc) rc = bgrow(b, &b->d_tiles, &b->cap_tiles, sizeof(BatchTile) * std::max<size_t>(1, order.size()));
+  if (!rc) rc = bgrow(b, &b->d_first, &b->cap_first, sizeof(int32_t) * first.size());
+  if (rc) return rc;
+  BCK(b, cudaMemcpyAsync(b->d_members, hm.data(), sizeof(M) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_tiles, order.data(), sizeof(BatchTile) * order.size(),
+                         cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_first, first.data(), sizeof(int32_t) * first.size(),
+                         cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));  // host vectors go out of scope
+  b->phase = 0;
+  drop_graph(b);
+  b->dirty = false;
+  return LBM_OK;
+}
+
+template <int Q, typename S> cudaError_t batch_launch(lbm_batch* b, int parity) {
+  using T = typename Codec<S>::T;
+  return launch_batch<Q, S>(static_cast<const BatchMember<T, S>*>(b->d_members),
+                            static_cast<const BatchTile*>(b->d_tiles),
+                            static_cast<const int32_t*>(b->d_first), b->nctas, parity, b->stream);
+}
+
+int batch_guard(lbm_batch* b) {
+  if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
+  if (b->poisoned) return bfail(b, LBM_ESTATE, "batch poisoned by an earlier CUDA error: %s", b->err.c_str());
+  return LBM_OK;
+}
+
+// Rebuilds the descriptors when a member changed (walls, stream) or was
+// stepped on its own since the last build.
+int batch_refresh(lbm_batch* b) {
+  if (!b->dirty) {
+    for (size_t i = 0; i < b->members.size(); ++i) {
+      const lbm_ctx* c = b->members[i];
+      if (c->version != b->versions[i] || c->cur != (b->cur0[i] ^ (int)(b->phase & 1))) {
+        b->dirty = true;
+        break;
+      }
+    }
+  }
+  if (!b->dirty) return LBM_OK;
+  for (lbm_ctx* c : b->members) {
+    if (c->poisoned) return bfail(b, LBM_ESTATE, "a member context is poisoned");
+    if (!c->has_state) return bfail(b, LBM_ESTATE, "a member has no populations");
+  }
+  return dispatch(b->Q, b->storage, [&]<int Q, typename S>() { return batch_build<Q, S>(b); });
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_allocator* a, void* cuda_stream, lbm_batch** out) {
+  if (!out) return bfail(nullptr, LBM_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (a && (!a->alloc || !a->free)) return bfail(nullptr, LBM_EINVAL, "allocator without alloc/free");
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation");
+  if (a) {
+    b->alloc = *a;
+    b->user_alloc = true;
+  }
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_add(lbm_batch* b, lbm_ctx* c) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  if (!c) return bfail(b, LBM_EINVAL, "null member");
+  if (std::find(b->members.begin(), b->members.end(), c) != b->members.end())
+    return bfail(b, LBM_EINVAL, "context already in the batch");
+  if (!b->members.empty() && (c->Q != b->Q || c->p.storage != b->storage))
+    return bfail(b, LBM_EINVAL, "members must share lattice and storage (batch: D2Q%d/%d, member: D2Q%d/%d)",
+                 b->Q, b->storage, c->Q, c->p.storage);
+  if (b->members.empty()) {
+    b->Q = c->Q;
+    b->storage = c->p.storage;
+  }
+  b->members.push_back(c);
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch* b, lbm_ctx* c) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  auto it = std::find(b->members.begin(), b->members.end(), c);
+  if (it == b->members.end()) return bfail(b, LBM_EINVAL, "context not in the batch");
+  b->members.erase(it);
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_size(const lbm_batch* b, int32_t* n) {
+  if (!b || !n) return bfail(nullptr, LBM_EINVAL, "null argument");
+  *n = (int32_t)b->members.size();
+  return LBM_OK;
+}
+
+int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  if (tile_rows < 0 || ctas < 0) return bfail(b, LBM_EINVAL, "negative tiling");
+  b->tile_rows = tile_rows;
+  b->ctas = ctas;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  if (nsteps < 0) return bfail(b, LBM_EINVAL, "negative step count");
+  if (b->members.empty() || nsteps == 0) return LBM_OK;
+  rc = batch_refresh(b);
+  if (rc) return rc;
+  // Work already enqueued on the members' own streams (initialisation,
+  // read-outs) completes before the batch touches their buffers.
+  if (!b->order_ev) BCK(b, cudaEventCreateWithFlags(&b->order_ev, cudaEventDisableTiming));
+  std::vector<cudaStream_t> mstreams;
+  for (lbm_ctx* c : b->members)
+    if (c->stream != b->stream &&
+        std::find(mstreams.begin(), mstreams.end(), c->stream) == mstreams.end())
+      mstreams.push_back(c->stream);
+  for (cudaStream_t ms : mstreams) {
+    BCK(b, cudaEventRecord(b->order_ev, ms));
+    BCK(b, cudaStreamWaitEvent(b->stream, b->order_ev, 0));
+  }
+  auto launch = [&](int parity) -> int {
+    return dispatch(b->Q, b->storage, [&]<int Q, typename S>() -> int {
+      BCK(b, batch_launch<Q, S>(b, parity));
+      return LBM_OK;
+    });
+  };
+  int64_t left = nsteps;
+  // Bring the phase to even, then replay a captured two-step graph.
+  if (b->phase & 1) {
+    if ((rc = launch(1))) return rc;
+    b->phase += 1;
+    left -= 1;
+  }
+  if (left >= 2 && b->stream != nullptr && !b->gexec) {
+    cudaGraph_t graph = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int r0 = launch(0), r1 = r0 ? r0 : launch(1);
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+    if (r0 || r1) {
+      if (graph) cudaGraphDestroy(graph);
+      return r0 ? r0 : r1;
+    }
+    BCK(b, ee);
+    cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    BCK(b, ei);
+  }
+  while (left >= 2) {
+    if (b->gexec) {
+      BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+    } else {
+      if ((rc = launch(0)) || (rc = launch(1))) return rc;
+    }
+    b->phase += 2;
+    left -= 2;
+  }
+  if (left == 1) {
+    if ((rc = launch(0))) return rc;
+    b->phase += 1;
+  }
+  // Later work on a member's stream sees the batch's steps.
+  BCK(b, cudaEventRecord(b->order_ev, b->stream));
+  for (cudaStream_t ms : mstreams) BCK(b, cudaStreamWaitEvent(ms, b->order_ev, 0));
+  for (lbm_ctx* c : b->members) {
+    c->cur ^= (int)(nsteps & 1);
+    c->steps += nsteps;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile_rows,
+                       int32_t* best_ctas, double* best_ms_per_step) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  if (b->members.empty() || steps_per_trial < 1) return bfail(b, LBM_EINVAL, "empty batch or no steps");
+  int dev = 0, sms = 0;
+  BCK(b, cudaGetDevice(&dev));
+  BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int cps = dispatch(b->Q, b->storage, [&]<int Q, typename S>() { return batch_ctas_per_sm<Q, S>(); });
+  const int rows_c[] = {4, 8, 16, 32, 64};
+  const int ctas_c[] = {0, std::max(1, cps) * sms};
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bt = b->tile_rows, bc = b->ctas;
+  for (int tr : rows_c) {
+    for (int ct : ctas_c) {
+      b->tile_rows = tr;
+      b->ctas = ct;
+      b->dirty = true;
+      if ((rc = lbm_batch_step(b, 2))) break;
+      cudaEventRecord(e0, b->stream);
+      if ((rc = lbm_batch_step(b, steps_per_trial))) break;
+      cudaEventRecord(e1, b->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = bfail(b, LBM_ECUDA, "autotune timing failed");
+        break;
+      }
+      const double per = ms / steps_per_trial;
+      if (per < best) {
+        best = per;
+        bt = tr;
+        bc = ct;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->tile_rows = bt;
+  b->ctas = bc;
+  b->dirty = true;
+  if (best_tile_rows) *best_tile_rows = bt;
+  if (best_ctas) *best_ctas = bc;
+  if (best_ms_per_step) *best_ms_per_step = best;
+  return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  cudaStreamSynchronize(b->stream);
+  cudaGetLastError();
+  drop_graph(b);
+  if (b->order_ev) cudaEventDestroy(b->order_ev);
+  bfree(b, b->d_members);
+  bfree(b, b->d_tiles);
+  bfree(b, b->d_first);
+  delete b;
+  return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"
+

@@ -47,10 +47,49 @@ template <int Q, typename S> int step_ctas_per_sm() {
   return n;
 }
 
+template <int Q, typename S>
+static cudaError_t prepare_batch_kernel() {
+  using Cfg = StepConfig<Q, S>;
+  using Sh = ConfigShape<Q, S>;
+  static cudaError_t once = cudaFuncSetAttribute(
+      batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>,
+      cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  return once;
+}
+
+template <int Q, typename S>
+cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
+                         const BatchTile* tiles, const int32_t* first, int nctas, int parity,
+                         cudaStream_t stream) {
+  using Cfg = StepConfig<Q, S>;
+  using Sh = ConfigShape<Q, S>;
+  cudaError_t e = prepare_batch_kernel<Q, S>();
+  if (e != cudaSuccess) return e;
+  batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>
+      <<<nctas, Cfg::W, Sh::SMEM, stream>>>(members, tiles, first, parity);
+  return cudaGetLastError();
+}
+
+template <int Q, typename S> int batch_ctas_per_sm() {
+  using Cfg = StepConfig<Q, S>;
+  using Sh = ConfigShape<Q, S>;
+  if (prepare_batch_kernel<Q, S>() != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>, Cfg::W, Sh::SMEM) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
 }  // namespace lbm
 
 #define LBM_INSTANTIATE_STEP(Q, S)                                                         \
   template cudaError_t lbm::launch_step<Q, S>(const CUtensorMap&, const CUtensorMap&,      \
                                               const lbm::StepArgs<lbm::Codec<S>::T, S>&,   \
                                               dim3, cudaStream_t, int);                    \
-  template int lbm::step_ctas_per_sm<Q, S>();
+  template int lbm::step_ctas_per_sm<Q, S>();                                            \
+  template cudaError_t lbm::launch_batch<Q, S>(                                          \
+      const lbm::BatchMember<lbm::Codec<S>::T, S>*, const lbm::BatchTile*, const int32_t*, \
+      int, int, cudaStream_t);                                                           \
+  template int lbm::batch_ctas_per_sm<Q, S>();

@@ -102,10 +102,57 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static_assert(Q % BD == 0, "box depth");
 };
 
-template <int Q, typename S, int W, int NS, int MODE, int MINB>
-__global__ void __launch_bounds__(W, MINB)
-    step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
-                const StepArgs<typename Codec<S>::T, S> a) {
+// Shared-memory carve-up of one CTA: NS stages, their mbarriers, the psi ring
+// and an abort flag.
+template <int Q, typename S, int W, int NS> struct StepSmem {
+  using Sh = StepShape<Q, S, W, NS>;
+  using T = typename Codec<S>::T;
+  unsigned char* stages;
+  uint64_t* bars;
+  T* ring;
+  int* s_abort;
+  __device__ static StepSmem carve(unsigned char* raw) {
+    StepSmem v;
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+    v.stages = base;
+    v.bars = reinterpret_cast<uint64_t*>(base + NS * Sh::STAGE);
+    v.ring = reinterpret_cast<T*>(v.bars + NS);
+    v.s_abort = reinterpret_cast<int*>(v.ring + Sh::RING_H * Sh::RING_W);
+    return v;
+  }
+};
+
+// Roles: the first lane of the last warp issues the TMA copies; the first
+// lanes of warps 0 and 1 form the left and right halo psi.
+template <int W> constexpr int kIssuer = W - 32;
+
+// Initialises the stage barriers (once per CTA) and returns the L2 policy the
+// issuer attaches to its loads.
+template <int Q, typename S, int W, int NS>
+__device__ __forceinline__ uint64_t step_smem_init(const StepSmem<Q, S, W, NS>& sm) {
+  uint64_t policy = 0;
+  if (threadIdx.x == kIssuer<W>) {
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) mbar_init(&sm.bars[s], 1);
+    *sm.s_abort = 0;
+    fence_barrier_init();
+    policy = l2_policy_evict_first();
+  }
+  __syncthreads();
+  return policy;
+}
+
+// Advances one strip segment of one lattice by a time step: node rows
+// [y0, y0 + Lr) of the W columns starting at x0.  `g` counts the rows this CTA
+// has pulled so far (stage g % NS, mbarrier phase (g / NS) & 1) and is
+// advanced by Lr + 2R, so a CTA may march several segments in turn.  Returns
+// false if a stage never arrived (the status word then has kStatusTimeout).
+template <int Q, typename S, int W, int NS, int MODE, typename Args>
+__device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUtensorMap* flg,
+                                              const Args& a, int x0, int y0, int Lr,
+                                              const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
+                                              uint64_t policy) {
   using Sh = StepShape<Q, S, W, NS>;
   using L = Lattice<Q>;
   using T = typename Codec<S>::T;
@@ -113,56 +160,43 @@ __global__ void __launch_bounds__(W, MINB)
   constexpr int R = Sh::R;
   constexpr int GX = Sh::GX;
   constexpr int GY = Sh::GY;
-
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  unsigned char* stages = base;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + NS * Sh::STAGE);
-  T* ring = reinterpret_cast<T*>(bars + NS);
-  int* s_abort = reinterpret_cast<int*>(ring + Sh::RING_H * Sh::RING_W);
+  unsigned char* const stages = sm.stages;
+  uint64_t* const bars = sm.bars;
+  T* const ring = sm.ring;
+  int* const s_abort = sm.s_abort;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int x0 = blockIdx.x * W;
-  const int y0 = blockIdx.y * a.tile_rows;
-  const int Lr = min(a.tile_rows, a.ny - y0);
   const int K = Lr + 2 * R;  // node rows y0 - R .. y0 + Lr + R - 1
   const int x = x0 + tid;
+  const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
+  const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
+  constexpr int kIss = kIssuer<W>;
 
-  // Roles: the first lane of the last warp issues the TMA copies; the first
-  // lanes of warps 0 and 1 form the left and right halo psi.
-  constexpr int kIssuer = W - 32;
-  uint64_t policy = 0;
-  if (tid == kIssuer) {
-    prefetch_tensormap(&src);
-    if (wall_on) prefetch_tensormap(&flg);
-#pragma unroll 1
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-    *s_abort = 0;
-    fence_barrier_init();
-    policy = l2_policy_evict_first();
-  }
+  // Every thread is done with the stages and ring of the previous segment.
   __syncthreads();
 
-  // The issuer copies node row k into stage k % NS: one box per plane group
-  // (the group's source row is y - c_y) plus, with walls, the row's flag words.
+  // The issuer copies node row k into stage (g0 + k) % NS: one box per plane
+  // group (the group's source row is y - c_y) plus, with walls, the row's flags.
   auto issue = [&](int k) {
-    const int s = k % NS;
+    const uint32_t gk = g0 + (uint32_t)k;
+    const int s = (int)(gk % NS);
     const int ynode = y0 - R + k;
     mbar_arrive_expect_tx(&bars[s], tx_bytes);
     unsigned char* st = stages + s * Sh::STAGE;
     static_for<0, Sh::NBOX>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
       constexpr int cy = Sh::kTab.box_cy[j];
-      tma_load_3d(st + j * Sh::BOXSLOT, &src, &bars[s], x0, ynode - cy + GY, j * Sh::BD, policy);
+      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD, policy);
     });
-    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, &flg, &bars[s], x0 >> 5, ynode);
+    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, flg, &bars[s], x0 >> 5, ynode);
   };
   int issued = 0;
-  if (tid == kIssuer) {
+  if (tid == kIss) {
+    prefetch_tensormap(src);
+    if (wall_on) prefetch_tensormap(flg);
     const int n0 = min(NS, K);
 #pragma unroll 1
     for (int k = 0; k < n0; ++k) issue(k);
@@ -194,11 +228,11 @@ __global__ void __launch_bounds__(W, MINB)
   int k = 0;
 #pragma unroll 1
   for (; k < K; ++k) {
-    const int s = k % NS;
-    if (!mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u)) *s_abort = 1;
+    const uint32_t gk = g0 + (uint32_t)k;
+    const int s = (int)(gk % NS);
+    if (!mbar_wait_bounded(&bars[s], (gk / NS) & 1u)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
-
     // Populations of the row collided in this iteration (row k - R).
     T f[Q];
     uint32_t flag;
@@ -232,7 +266,7 @@ __global__ void __launch_bounds__(W, MINB)
     if (*s_abort) break;
 
     // Every thread has finished iteration k - 1: recycle the stage it last used.
-    if (tid == kIssuer) {
+    if (tid == kIss) {
       const int fr = k - 1 - (Sh::kRegs ? 0 : R);
       if (fr >= 0 && fr + NS < K) {
         issue(fr + NS);
@@ -244,7 +278,7 @@ __global__ void __launch_bounds__(W, MINB)
       const int ko = k - R;
       const int yo = y0 - R + ko;
       if constexpr (!Sh::kRegs) {
-        const unsigned char* sto = stages + (ko % NS) * Sh::STAGE;
+        const unsigned char* sto = stages + (int)((g0 + (uint32_t)ko) % NS) * Sh::STAGE;
         static_for<0, Q>([&](auto ic) {
           f[decltype(ic)::value] = load_pop(reinterpret_cast<const S*>(sto), ic, tid);
         });
@@ -299,7 +333,10 @@ __global__ void __launch_bounds__(W, MINB)
             constexpr int i = decltype(ic)::value;
             out[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i], T(L::w(i)) * rho_s);
           });
-          const bool edge = x < GX || x >= a.nx - GX || yo < GY || yo >= a.ny - GY;
+          // Periodic images exist only for nodes within GX of a side or GY of
+          // the top or bottom; the strip test is per CTA, the row test per row.
+          const bool edge = (strip_edge && (x < GX || x >= a.nx - GX)) || yo < GY ||
+                            yo >= a.ny - GY;
           if (edge) {
             int xa = x;
             while (xa - a.nx >= -GX) xa -= a.nx;
@@ -333,13 +370,77 @@ __global__ void __launch_bounds__(W, MINB)
     }
   }
 
+  g = g0 + (uint32_t)K;
   if (*s_abort) {
     // A stage never completed.  Record it, then give the copies still in
-    // flight a bounded chance to land before the CTA's shared memory goes away.
-    if (tid == kIssuer) {
+    // flight a bounded chance to land before the shared memory is reused.
+    if (tid == kIss) {
       atomicOr(a.status, kStatusTimeout);
-      for (int r = k; r < issued; ++r) mbar_wait_bounded(&bars[r % NS], (uint32_t)(r / NS) & 1u);
+      for (int r = k; r < issued; ++r) {
+        const uint32_t gr = g0 + (uint32_t)r;
+        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u);
+      }
     }
+    return false;
+  }
+  return true;
+}
+
+// One time step of one lattice: CTA (bx, by) marches strip bx, segment by.
+template <int Q, typename S, int W, int NS, int MODE, int MINB>
+__global__ void __launch_bounds__(W, MINB)
+    step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
+                const StepArgs<typename Codec<S>::T, S> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
+  const uint64_t policy = step_smem_init(sm);
+  const int y0 = blockIdx.y * a.tile_rows;
+  uint32_t g = 0;
+  march_segment<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
+                                   sm, g, policy);
+}
+
+// A lattice of a batch: TMA maps of its two population buffers and of its wall
+// flags, and the step arguments for either direction (args[d] reads buffer d
+// and writes buffer 1 - d).  cur: the buffer holding the state at parity 0.
+template <typename T, typename S> struct alignas(64) BatchMember {
+  CUtensorMap map[2];
+  CUtensorMap flags;
+  StepArgs<T, S> args[2];
+  int32_t cur;
+};
+
+// One segment of one member lattice.
+struct BatchTile {
+  int32_t member, x0, y0, rows;
+};
+
+// One time step of every lattice of a batch.  CTA b marches tiles
+// [first[b], first[b + 1]) in order; `parity` flips the read/write buffers on
+// alternate steps.
+template <int Q, typename S, int W, int NS, int MINB>
+__global__ void __launch_bounds__(W, MINB)
+    batch_step_kernel(const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
+                      const BatchTile* __restrict__ tiles, const int32_t* __restrict__ first,
+                      int32_t parity) {
+  using Args = StepArgs<typename Codec<S>::T, S>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ Args s_args;
+  const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
+  const uint64_t policy = step_smem_init(sm);
+  uint32_t g = 0;
+  const int t1 = first[blockIdx.x + 1];
+#pragma unroll 1
+  for (int t = first[blockIdx.x]; t < t1; ++t) {
+    const BatchTile tile = tiles[t];
+    const auto* m = &members[tile.member];
+    const int dir = (m->cur ^ parity) & 1;
+    __syncthreads();  // the previous tile no longer reads s_args
+    if (threadIdx.x == 0) s_args = m->args[dir];
+    __syncthreads();
+    if (!march_segment<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
+                                              tile.rows, sm, g, policy))
+      return;
   }
 }
 

@@ -185,6 +185,65 @@ class Simulation:
         return sim
 
 
+class Batch:
+    """Several Simulations of one (lattice, storage) kind advanced together, one
+    fused launch per time step (lbm_batch_* of include/lbm.h)."""
+
+    def __init__(self, stream=None, use_torch_allocator: bool = True, device=None):
+        """``stream``: the stream batch steps run on; by default a new stream, so
+        that two steps can be captured in a CUDA graph.  Each step is ordered
+        with the members' streams by the library (events both ways)."""
+        import torch
+        self.lib = L.load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.allocator = TorchAllocator(dev) if use_torch_allocator else None
+        h = ctypes.c_void_p()
+        L.check_batch(self.lib.lbm_batch_create(
+            ctypes.byref(self.allocator.struct) if self.allocator else None,
+            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.members = []
+
+    def _chk(self, rc):
+        L.check_batch(rc, self.h)
+
+    def add(self, sim: "Simulation"):
+        self._chk(self.lib.lbm_batch_add(self.h, sim.ctx))
+        self.members.append(sim)
+
+    def remove(self, sim: "Simulation"):
+        self.stream.synchronize()
+        self._chk(self.lib.lbm_batch_remove(self.h, sim.ctx))
+        self.members.remove(sim)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def set_tiling(self, tile_rows: int = 0, ctas: int = 0):
+        self._chk(self.lib.lbm_batch_set_tiling(self.h, int(tile_rows), int(ctas)))
+
+    def step(self, n: int = 1):
+        self._chk(self.lib.lbm_batch_step(self.h, int(n)))
+
+    def autotune(self, steps_per_trial: int = 20):
+        tr, ct, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        self._chk(self.lib.lbm_batch_autotune(self.h, int(steps_per_trial), ctypes.byref(tr),
+                                              ctypes.byref(ct), ctypes.byref(ms)))
+        return dict(tile_rows=tr.value, ctas=ct.value, ms_per_step=ms.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def wall_gaussian_filter(solid: np.ndarray, lattice: int = 21, n_rep: int = 5, n_att: int = 22):
     """Appendix wall functions on the device: returns (phi_S, psi_R-bar, psi_A-bar)."""
     lib = L.load()

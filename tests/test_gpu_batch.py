@@ -1,0 +1,98 @@
+"""Batches: many lattices advanced by one fused launch per step.
+
+Each member's node arithmetic is the same as when it runs alone, so a member's
+populations after n batch steps must equal, bit for bit, those after n steps on
+its own -- for every tiling, with persistent CTAs, across odd step counts (the
+two-step graph plus a single launch) and when members are stepped on their
+own or removed between batch steps."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1202_6130_gb300 as p
+    p.load()
+    return p
+
+
+def _cases():
+    out = []
+    for k, (nx, ny) in enumerate([(64, 32), (200, 90), (131, 47), (300, 160), (8, 8), (257, 33)]):
+        w = W.droplet_on_wall(nx=nx, ny=ny, R=min(nx, ny) / 3.0, seed=20 + k, noise_amp=1e-5,
+                              tau=0.7 + 0.15 * k, G=-5.0 - 0.2 * k, G_A=0.02 * k, G_R=0.15 - 0.02 * k)
+        if k % 2 == 1:
+            uw = np.zeros((2, ny, nx))
+            uw[0, ny // 2:, :] = 0.01
+            w.u_wall = uw
+        if k == 3:
+            w.body_force = (2e-6, 0.0)
+        out.append(w)
+    return out
+
+
+def _alone(pkg, w, storage, n):
+    sim = pkg.Simulation.from_workload(w, storage=storage)
+    sim.step(n)
+    f = sim.populations()
+    sim.close()
+    return f
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("tiling", [(0, 0), (8, 0), (16, 300), (5, 7)])
+def test_batch_equals_members_alone_bitwise(pkg, storage, tiling):
+    ws = _cases()
+    n1, n2 = 7, 10  # odd then even: single launch, graph replays, phase carry-over
+    want = [_alone(pkg, w, storage, n1 + n2) for w in ws]
+    sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
+    b = pkg.Batch()
+    for s in sims:
+        b.add(s)
+    b.set_tiling(*tiling)
+    b.step(n1)
+    b.step(n2)
+    for s, f in zip(sims, want):
+        np.testing.assert_array_equal(s.populations(), f)
+        assert s.steps_done() == n1 + n2
+    b.close()
+
+
+def test_members_stepped_alone_or_removed_between_batch_steps(pkg):
+    ws = _cases()[:4]
+    sims = [pkg.Simulation.from_workload(w, storage="fp64") for w in ws]
+    b = pkg.Batch()
+    for s in sims:
+        b.add(s)
+    b.step(3)
+    sims[1].step(2)          # member advanced on its own
+    b.step(4)
+    b.remove(sims[2])        # sims[2] stays at 7 steps
+    b.step(1)
+    expect = {0: 8, 1: 10, 2: 7, 3: 8}
+    for i, s in enumerate(sims):
+        assert s.steps_done() == expect[i]
+        np.testing.assert_array_equal(s.populations(), _alone(pkg, ws[i], "fp64", expect[i]))
+    b.close()
+
+
+def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
+    ws = _cases()[:3]
+    a = pkg.Simulation.from_workload(ws[0], storage="fp32")
+    c = pkg.Simulation.from_workload(ws[1], storage="fp64")
+    b = pkg.Batch()
+    b.add(a)
+    with pytest.raises(pkg.LbmError):
+        b.add(c)
+    b.add(pkg.Simulation.from_workload(ws[2], storage="fp32"))
+    best = b.autotune(steps_per_trial=4)
+    assert best["tile_rows"] in (4, 8, 16, 32, 64) and best["ms_per_step"] > 0
+    b.step(3)
+    assert np.isfinite(a.moments()[0]).all()
+    b.close()
