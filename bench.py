@@ -170,54 +170,59 @@ def barrier(world: int):
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(rows: int, steps: int):
-    """Runs the FP64 oracle on rows [0, rows) of the workload (a periodic band of
-    the full width, wall included); returns (node updates, seconds)."""
-    import numpy as np
-    import workloads as W
-    from oracle import lbm_oracle as O
-    w = W.large_multi_droplet(with_fields=False)
-    T = 3.0 + 1.5 * np.sin(2.0 * np.pi * 8.0 * np.arange(NX) / NX)
-    rho = W.droplet_density(NX, rows, w.meta["centers"], w.meta["radii"], 2.0, 0.15, 2.0)
-    phi, pr, pa = W.wall_core_tail(W.wall_distance_slab(NX, rows), T[None, :])
-    p = O.Params(lattice=O.D2Q9, tau=1.0, G=-5.5)
-    wall = O.Wall(phi, pr, pa, 0.1, 0.05, 1.0)
-    z = np.zeros_like(rho)
-    f = O.initial_populations(p, rho, z, z)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        f = O.step(p, wall, f)
-    dt = time.perf_counter() - t0
-    return NX * rows * steps, dt
+class OracleBand:
+    """The FP64 oracle on rows [0, rows) of the workload: a periodic band of the
+    full 8192-wide lattice with its wall (the sample the CPU legs time)."""
+
+    def __init__(self, rows: int):
+        import workloads as W
+        from oracle import lbm_oracle as O
+        self.O = O
+        w = W.large_multi_droplet(with_fields=False)
+        T = 3.0 + 1.5 * np.sin(2.0 * np.pi * 8.0 * np.arange(NX) / NX)
+        rho = W.droplet_density(NX, rows, w.meta["centers"], w.meta["radii"], 2.0, 0.15, 2.0)
+        phi, pr, pa = W.wall_core_tail(W.wall_distance_slab(NX, rows), T[None, :])
+        self.p = O.Params(lattice=O.D2Q9, tau=1.0, G=-5.5)
+        self.wall = O.Wall(phi, pr, pa, 0.1, 0.05, 1.0)
+        z = np.zeros_like(rho)
+        self.f = O.initial_populations(self.p, rho, z, z)
+        self.nodes = NX * rows
+
+    def step(self, n: int = 1) -> float:
+        """Runs n oracle steps; returns their wall time in seconds."""
+        t0 = time.perf_counter()
+        for _ in range(n):
+            self.f = self.O.step(self.p, self.wall, self.f)
+        return time.perf_counter() - t0
 
 
 def cpu_baseline(target_s: float = 15.0):
     rows = 256
-    n, dt = oracle_sample(rows, 1)
-    steps = max(1, int(target_s / max(dt, 1e-3)))
-    n, dt = oracle_sample(rows, steps)
-    return {"value": n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    band = OracleBand(rows)
+    dt1 = band.step(1)
+    steps = max(1, int(target_s / max(dt1, 1e-3)))
+    dt = band.step(steps)
+    return {"value": band.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"FP64 numpy oracle, rows 0..{rows - 1} of the 8192-wide workload as a "
                       f"periodic {NX}x{rows} band with its wall, {steps} steps, one thread"}
 
 
 def run_reference(args, world, rank):
+    """The FP64 oracle as the reference arm: each bench step is one oracle step
+    on a periodic 8192-wide band of the workload, sized so that warm-up plus
+    timed steps take about two and a half minutes of one host thread."""
     if rank != 0:
         return 0
     budget = 150.0
     total = args.steps + args.warmup
-    # calibrate: seconds per node-step of the oracle on this host
-    n, dt = oracle_sample(16, 1)
-    per = dt / n
-    rows = int(max(4, min(512, budget / total / per / NX)))
-    for _ in range(args.warmup):
-        oracle_sample(rows, 1)
-    n, dt = 0, 0.0
-    for _ in range(args.steps):
-        a, b = oracle_sample(rows, 1)
-        n += a
-        dt += b
-    v = n / dt / 1e6
+    probe = OracleBand(16)
+    probe.step(1)
+    per_node = probe.step(2) / (2 * probe.nodes)
+    rows = int(max(4, min(512, budget / total / per_node / NX)))
+    band = OracleBand(rows)
+    band.step(args.warmup)
+    dt = band.step(args.steps)
+    v = band.nodes * args.steps / dt / 1e6
     line = {
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
