@@ -179,16 +179,18 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
   return LBM_OK;
 }
 
-// Rows per CTA segment.  Measured on GB300 (8192x4096 D2Q9): short segments
-// win although their 2R halo rows are re-read (from L2), because many waves of
-// short CTAs keep the concurrently active tiles in a compact band of rows and
-// balance the SMs dynamically; FP32 is fastest near 8 rows, 16-bit storage
-// near 24-48.  Small lattices get shorter segments so that the grid still
-// covers at least two waves of resident CTAs.
-int choose_tile_rows(int nx, int ny, int W, int esize, int ctas_per_sm, int num_sms) {
+// Rows per CTA segment.  Measured on GB300 (8192x4096 D2Q9 sweep): short
+// segments run fastest -- many waves of short CTAs keep the concurrently
+// active tiles in a compact band of rows and balance the SMs dynamically, and
+// the 2R halo rows a segment shares with the one below are then still in L2.
+// FP32 is fastest near 24 rows, 16-bit storage near 48, FP64 near 64.  Small
+// lattices get shorter segments so that the grid still covers at least two
+// waves of resident CTAs.
+int choose_tile_rows(int nx, int ny, int W, int esize, int R, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  int L = esize == 2 ? 32 : (esize == 4 ? 8 : 32);
+  int L = esize == 2 ? 48 : (esize == 4 ? 24 : 64);
+  if (R > 1) L = std::max(L, 16 * R);
   while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
   return std::max(1, std::min(L, ny));
 }
@@ -222,7 +224,7 @@ template <int Q, typename S> int setup_layout(lbm_ctx* c) {
     return fail(c, LBM_ECUDA, "step kernel cannot be resident (%s)", cudaGetErrorString(e));
   }
   c->tile_rows = c->p.tile_rows > 0 ? std::min(c->p.tile_rows, c->p.ny)
-                                    : choose_tile_rows(c->p.nx, c->p.ny, c->W, c->esize, cps, sms);
+                                    : choose_tile_rows(c->p.nx, c->p.ny, c->W, c->esize, c->R, cps, sms);
   c->grid_x = (c->p.nx + c->W - 1) / c->W;
   c->grid_y = (c->p.ny + c->tile_rows - 1) / c->tile_rows;
   return LBM_OK;

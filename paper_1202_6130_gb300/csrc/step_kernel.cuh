@@ -189,7 +189,9 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
     static_for<0, Sh::NBOX>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
       constexpr int cy = Sh::kTab.box_cy[j];
-      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD, policy);
+      // Normal L2 priority: the 2R halo rows of a segment are read again by
+      // the segment below a few microseconds later and should hit in L2.
+      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD);
     });
     if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, flg, &bars[s], x0 >> 5, ynode);
   };
