@@ -242,6 +242,37 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def measure_serving(pkg, torch, W, n: int = 32, storage: str = "fp32"):
+    """Continuous-batching serving against plain sequential solves, on the
+    first n requests of the Poisson stream (seed 3; sizes log-uniform 64x32 ..
+    2048x1024, budgets 1k..20k steps, random wall parameters).  Two arrival
+    rates: the specified 2000 req/s (a burst: throughput and queueing) and
+    10 req/s (a load the GPU sustains, so p50/p99 reflect service, not backlog).
+    Time-to-result runs from a request's arrival to its measured result
+    (contact angle or slip length) on the host."""
+    from paper_1202_6130_gb300 import serve
+    out = {"requests": n, "storage": storage}
+    for label, rate in (("burst_2000_per_s", 2000.0), ("sustained_10_per_s", 10.0)):
+        reqs = serve.requests_from_stream(W.serving_stream(rate=rate, duration=1e9, seed=3,
+                                                           max_requests=n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        srv = serve.Server(storage=storage, hbm_budget=100e9, quantum=500)
+        res_b = srv.run(reqs, realtime=True)
+        srv.close()
+        t_b = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res_s = serve.run_sequential(reqs, storage=storage, realtime=True)
+        t_s = time.perf_counter() - t0
+        b = serve.summarize(res_b, t_b)
+        q = serve.summarize(res_s, t_s)
+        same = all(x.value == y.value or (x.value != x.value and y.value != y.value)
+                   for x, y in zip(sorted(res_b, key=lambda r: r.id), sorted(res_s, key=lambda r: r.id)))
+        out[label] = {"rate_per_s": rate, "batched": b, "sequential": q,
+                      "throughput_ratio": b["mlups"] / q["mlups"], "results_identical": same}
+    return out
+
+
 def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: int = 256):
     """The batched parameter sweep: n independent lattices, sizes log-uniform in
     64x32 .. 1024x512 (seed 2), each with its own tau, G, G_R, G_A and a drop or
@@ -372,6 +403,8 @@ def run_gpu(args, world, rank, local):
     }
     if not args.no_batch:
         line["batch"] = measure_batch(pkg, torch, W)
+    if not args.no_serving:
+        line["serving"] = measure_serving(pkg, torch, W)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -388,6 +421,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched parameter-sweep measurement")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the continuous-batching serving measurement")
     ap.add_argument("--size", default=f"{NX}x{NY}",
                     help="lattice size NXxNY (the same recipe at another size, for profiling)")
     args = ap.parse_args(argv)

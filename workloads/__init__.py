@@ -246,6 +246,8 @@ def serving_stream(rate: float = 2000.0, duration: float = 60.0, seed: int = 3,
     arrival time, kind, nx, ny, steps and wall parameters (fields are built
     lazily by the caller with ``droplet_on_wall`` / ``poiseuille_channel``)."""
     n_est = int(rate * duration * 1.5) + 16
+    if max_requests is not None:
+        n_est = min(n_est, max_requests)
     u = uniform(seed, 6 * n_est, 0.0, 1.0).reshape(n_est, 6)
     t = 0.0
     reqs = []
