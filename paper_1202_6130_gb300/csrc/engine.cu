@@ -183,13 +183,13 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
 // segments run fastest -- many waves of short CTAs keep the concurrently
 // active tiles in a compact band of rows and balance the SMs dynamically, and
 // the 2R halo rows a segment shares with the one below are then still in L2.
-// FP32 is fastest near 24 rows, 16-bit storage near 48, FP64 near 64.  Small
+// FP32 is fastest near 12-24 rows, 16-bit storage near 24, FP64 near 64.  Small
 // lattices get shorter segments so that the grid still covers at least two
 // waves of resident CTAs.
 int choose_tile_rows(int nx, int ny, int W, int esize, int R, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  int L = esize == 2 ? 48 : (esize == 4 ? 24 : 64);
+  int L = esize == 2 ? 24 : (esize == 4 ? 16 : 64);
   if (R > 1) L = std::max(L, 16 * R);
   while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
   return std::max(1, std::min(L, ny));

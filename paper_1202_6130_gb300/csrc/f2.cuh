@@ -1,0 +1,77 @@
+// Two-lane FP32 arithmetic for kernels that update two nodes per thread.
+// Every operation maps to one packed instruction of the sm_100 family
+// (fma.rn.f32x2, add.rn.f32x2, mul.rn.f32x2), each lane rounded exactly as
+// the scalar operation would be.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+struct F2 {
+  float2 v;
+  __device__ __forceinline__ F2() = default;
+  __device__ __forceinline__ F2(float2 a) : v(a) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ static F2 splat(float a) { return F2(a, a); }
+  __device__ __forceinline__ float x() const { return v.x; }
+  __device__ __forceinline__ float y() const { return v.y; }
+};
+
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  return F2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y)));
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) { return a = a - b; }
+
+// c * v for a compile-time lattice coefficient c.
+template <int C> __device__ __forceinline__ F2 cmul2(F2 v) {
+  if constexpr (C == 0) return F2::splat(0.f);
+  else if constexpr (C == 1) return v;
+  else if constexpr (C == -1) return -v;
+  else return v * F2::splat((float)C);
+}
+template <int CX, int CY> __device__ __forceinline__ F2 cdot2(F2 ux, F2 uy) {
+  if constexpr (CX == 0) return cmul2<CY>(uy);
+  else if constexpr (CY == 0) return cmul2<CX>(ux);
+  else return cmul2<CX>(ux) + cmul2<CY>(uy);
+}
+
+// Two adjacent stored values as an F2.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+  using Raw = float2;
+  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(r); }
+  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) { return f.v; }
+  __device__ __forceinline__ static F2 dec1(float a, float b, F2 wrs) { return F2(a, b); }
+};
+template <> struct Pair<__half> {
+  using Raw = __half2;
+  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(__half22float2(r)) + wrs; }
+  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
+    const F2 d = f - wrs;
+    return __floats2half2_rn(d.x(), d.y());
+  }
+  __device__ __forceinline__ static F2 dec1(__half a, __half b, F2 wrs) {
+    return F2(__half2float(a), __half2float(b)) + wrs;
+  }
+};
+template <> struct Pair<__nv_bfloat16> {
+  using Raw = __nv_bfloat162;
+  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(__bfloat1622float2(r)) + wrs; }
+  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
+    const F2 d = f - wrs;
+    return __floats2bfloat162_rn(d.x(), d.y());
+  }
+  __device__ __forceinline__ static F2 dec1(__nv_bfloat16 a, __nv_bfloat16 b, F2 wrs) {
+    return F2(__bfloat162float(a), __bfloat162float(b)) + wrs;
+  }
+};
+
+}  // namespace lbm

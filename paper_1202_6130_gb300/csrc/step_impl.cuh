@@ -26,11 +26,11 @@ cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
   if (mode == kModeStep) {
     if ((e = prepare_kernel<Q, S, kModeStep>()) != cudaSuccess) return e;
     step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>
-        <<<grid, Cfg::W, Sh::SMEM, stream>>>(src, flags, a);
+        <<<grid, Sh::NT, Sh::SMEM, stream>>>(src, flags, a);
   } else {
     if ((e = prepare_kernel<Q, S, kModeMoments>()) != cudaSuccess) return e;
     step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments, Cfg::MINB>
-        <<<grid, Cfg::W, Sh::SMEM, stream>>>(src, flags, a);
+        <<<grid, Sh::NT, Sh::SMEM, stream>>>(src, flags, a);
   }
   return cudaGetLastError();
 }
@@ -41,7 +41,7 @@ template <int Q, typename S> int step_ctas_per_sm() {
   if (prepare_kernel<Q, S, kModeStep>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, Cfg::W, Sh::SMEM) !=
+          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, Sh::NT, Sh::SMEM) !=
       cudaSuccess)
     return 0;
   return n;
@@ -66,7 +66,7 @@ cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
   cudaError_t e = prepare_batch_kernel<Q, S>();
   if (e != cudaSuccess) return e;
   batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>
-      <<<nctas, Cfg::W, Sh::SMEM, stream>>>(members, tiles, first, parity);
+      <<<nctas, Sh::NT, Sh::SMEM, stream>>>(members, tiles, first, parity);
   return cudaGetLastError();
 }
 
@@ -76,7 +76,7 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   if (prepare_batch_kernel<Q, S>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>, Cfg::W, Sh::SMEM) !=
+          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>, Sh::NT, Sh::SMEM) !=
       cudaSuccess)
     return 0;
   return n;

@@ -27,6 +27,7 @@
 
 #include <cuda.h>
 
+#include "f2.cuh"
 #include "lattice.cuh"
 #include "node.cuh"
 #include "tma.cuh"
@@ -72,7 +73,12 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int CHUNKS = W / 32;  // wall-flag words per row
   static constexpr int FLAG_SLOT = ((CHUNKS * 4 + 127) / 128) * 128;
   static constexpr int STAGE = NBOX * BOXSLOT + FLAG_SLOT;
-  static constexpr int RING_W = W + 2 * R;
+  // Nodes per thread: D2Q9 with FP32 arithmetic updates two adjacent columns
+  // per thread with packed FP32 instructions; otherwise one.
+  static constexpr int V = (Q == 9 && sizeof(T) == 4) ? 2 : 1;
+  static constexpr int NT = W / V;                       // threads per CTA
+  static constexpr int RO = V == 2 ? 2 : R;              // ring column of node 0 (even for V = 2)
+  static constexpr int RING_W = W + 2 * RO;
   static constexpr int RING_H = 2 * R + 2;
   static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
                               RING_H * RING_W * (int)sizeof(T) + 16;
@@ -98,6 +104,7 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   }
   static constexpr Tables kTab = make_tables();
   static_assert(W % 32 == 0 && W >= 64 && CHUNKS <= 256, "strip width");
+  static_assert(NT % 32 == 0 && NT >= 64, "threads per CTA");
   static_assert(NS >= R + 2, "pipeline depth");
   static_assert(Q % BD == 0, "box depth");
 };
@@ -125,14 +132,14 @@ template <int Q, typename S, int W, int NS> struct StepSmem {
 
 // Roles: the first lane of the last warp issues the TMA copies; the first
 // lanes of warps 0 and 1 form the left and right halo psi.
-template <int W> constexpr int kIssuer = W - 32;
+template <int NT> constexpr int kIssuer = NT - 32;
 
 // Initialises the stage barriers (once per CTA) and returns the L2 policy the
 // issuer attaches to its loads.
 template <int Q, typename S, int W, int NS>
 __device__ __forceinline__ uint64_t step_smem_init(const StepSmem<Q, S, W, NS>& sm) {
   uint64_t policy = 0;
-  if (threadIdx.x == kIssuer<W>) {
+  if (threadIdx.x == kIssuer<StepShape<Q, S, W, NS>::NT>) {
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) mbar_init(&sm.bars[s], 1);
     *sm.s_abort = 0;
@@ -173,7 +180,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
-  constexpr int kIss = kIssuer<W>;
+  constexpr int kIss = kIssuer<Sh::NT>;
 
   // Every thread is done with the stages and ring of the previous segment.
   __syncthreads();
@@ -227,12 +234,15 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
 
   T fnext[Q];            // kRegs: populations of the row whose psi was just formed
   uint32_t flag_next = 0;
+  // Stage and mbarrier phase of row k, advanced incrementally.
+  int s = (int)(g0 % NS);
+  uint32_t phase = (g0 / NS) & 1u;
   int k = 0;
-#pragma unroll 1
+  // Unrolled by two so that the populations carried from one row to the next
+  // (kRegs) alternate between register sets instead of being copied.
+#pragma unroll 2
   for (; k < K; ++k) {
-    const uint32_t gk = g0 + (uint32_t)k;
-    const int s = (int)(gk % NS);
-    if (!mbar_wait_bounded(&bars[s], (gk / NS) & 1u)) *s_abort = 1;
+    if (!mbar_wait_bounded(&bars[s], phase)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
     // Populations of the row collided in this iteration (row k - R).
@@ -254,14 +264,14 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
         if constexpr (Sh::kRegs) fnext[i] = v;
         rho = (i == 0) ? v : rho + v;
       });
-      ring_row[tid + R] = pseudo_potential<Q, T>(a.phys, rho);
+      ring_row[tid + Sh::RO] = pseudo_potential<Q, T>(a.phys, rho);
       if constexpr (Sh::kRegs) flag_next = flags_of(stb);
     }
     {
       const int lane = tid & 31;
       if (warp < 2 && lane < R) {
         const int xl = warp == 0 ? lane - R : W + lane;
-        ring_row[xl + R] = psi_at(st, xl);
+        ring_row[xl + Sh::RO] = psi_at(st, xl);
       }
     }
     __syncthreads();
@@ -280,7 +290,8 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       const int ko = k - R;
       const int yo = y0 - R + ko;
       if constexpr (!Sh::kRegs) {
-        const unsigned char* sto = stages + (int)((g0 + (uint32_t)ko) % NS) * Sh::STAGE;
+        const int so = s >= R ? s - R : s - R + NS;  // stage of row k - R
+        const unsigned char* sto = stages + so * Sh::STAGE;
         static_for<0, Q>([&](auto ic) {
           f[decltype(ic)::value] = load_pop(reinterpret_cast<const S*>(sto), ic, tid);
         });
@@ -293,12 +304,12 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       const T uy = div_rho<T>(jy, rho, inv_rho);
 
       // sum_i w_i psi(x + c_i) c_i from the ring (rest state contributes 0).
-      const T psi_c = ring[(ko % Sh::RING_H) * Sh::RING_W + tid + R];
+      const T psi_c = ring[(ko % Sh::RING_H) * Sh::RING_W + tid + Sh::RO];
       T sfx = 0, sfy = 0;
       static_for<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         if constexpr (L::cx(i) != 0 || L::cy(i) != 0) {
-          const T nb = ring[((ko + L::cy(i)) % Sh::RING_H) * Sh::RING_W + tid + R + L::cx(i)];
+          const T nb = ring[((ko + L::cy(i)) % Sh::RING_H) * Sh::RING_W + tid + Sh::RO + L::cx(i)];
           const T wn = T(L::w(i)) * nb;
           if constexpr (L::cx(i) != 0) sfx += cmul<L::cx(i)>(wn);
           if constexpr (L::cy(i) != 0) sfy += cmul<L::cy(i)>(wn);
@@ -370,6 +381,10 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
         }
       }
     }
+    if (++s == NS) {
+      s = 0;
+      phase ^= 1u;
+    }
   }
 
   g = g0 + (uint32_t)K;
@@ -388,9 +403,369 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   return true;
 }
 
+// Two nodes per thread (D2Q9, FP32 arithmetic): thread t updates columns 2t
+// and 2t + 1 of the strip.  Same schedule and stage layout as march_segment;
+// the node arithmetic runs on packed FP32 pairs, aligned pairs of stored
+// populations and of psi are moved with one 64- or 32-bit access, and each
+// population row is stored as pairs.  Wall terms, ghost images, the halo psi
+// and a pair that straddles the lattice's right edge fall back to per-node
+// code.
+template <typename S, int W, int NS, int MODE, typename Args>
+__device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const CUtensorMap* flg,
+                                                 const Args& a, int x0, int y0, int Lr,
+                                                 const StepSmem<9, S, W, NS>& sm, uint32_t& g) {
+  constexpr int Q = 9;
+  using Sh = StepShape<Q, S, W, NS>;
+  using L = Lattice<Q>;
+  using E = EqConst<Q>;
+  using C = Codec<S>;
+  using PR = Pair<S>;
+  using T = float;
+  constexpr int R = 1;
+  constexpr int GX = Sh::GX;
+  constexpr int GY = Sh::GY;
+  constexpr int RO = Sh::RO;
+  static_assert(Sh::V == 2 && Sh::kRegs, "two-node march");
+  unsigned char* const stages = sm.stages;
+  uint64_t* const bars = sm.bars;
+  T* const ring = sm.ring;
+  int* const s_abort = sm.s_abort;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int xa = 2 * tid;      // first of the thread's two columns, relative to x0
+  const int x = x0 + xa;
+  const int K = Lr + 2 * R;
+  const uint32_t g0 = g;
+  const bool wall_on = a.wall.active != 0;
+  const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
+  const bool pair_ok = x + 1 < a.nx;  // both nodes exist
+  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
+  constexpr int kIss = kIssuer<Sh::NT>;
+
+  __syncthreads();
+
+  auto issue = [&](int k) {
+    const uint32_t gk = g0 + (uint32_t)k;
+    const int s = (int)(gk % NS);
+    const int ynode = y0 - R + k;
+    mbar_arrive_expect_tx(&bars[s], tx_bytes);
+    unsigned char* st = stages + s * Sh::STAGE;
+    static_for<0, Sh::NBOX>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      constexpr int cy = Sh::kTab.box_cy[j];
+      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD);
+    });
+    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, flg, &bars[s], x0 >> 5, ynode);
+  };
+  int issued = 0;
+  if (tid == kIss) {
+    prefetch_tensormap(src);
+    if (wall_on) prefetch_tensormap(flg);
+    const int n0 = min(NS, K);
+#pragma unroll 1
+    for (int k = 0; k < n0; ++k) issue(k);
+    issued = n0;
+  }
+
+  const T rho_s = a.phys.rho_s;
+  // Population I of the thread's two columns: an aligned pair when c_x is even
+  // (one access), else two single loads.
+  auto load_pair = [&](const S* st, auto ic) -> F2 {
+    constexpr int i = decltype(ic)::value;
+    constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
+    const F2 wrs = F2::splat(T(L::w(i)) * rho_s);
+    if constexpr ((off & 1) == 0) {
+      return PR::dec(*reinterpret_cast<const typename PR::Raw*>(st + off + xa), wrs);
+    } else {
+      return PR::dec1(st[off + xa], st[off + xa + 1], wrs);
+    }
+  };
+  auto psi_at = [&](const S* st, int xl) -> T {  // one node (halo columns)
+    T rho = 0;
+    static_for<0, Q>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
+      const T v = C::dec(st[off + xl], T(L::w(i)) * rho_s);
+      rho = (i == 0) ? v : rho + v;
+    });
+    return pseudo_potential<Q, T>(a.phys, rho);
+  };
+
+  F2 fnext[Q];
+  uint32_t flag_next = 0;
+  int s = (int)(g0 % NS);
+  uint32_t phase = (g0 / NS) & 1u;
+  int k = 0;
+#pragma unroll 2
+  for (; k < K; ++k) {
+    if (!mbar_wait_bounded(&bars[s], phase)) *s_abort = 1;
+    const unsigned char* stb = stages + s * Sh::STAGE;
+    const S* st = reinterpret_cast<const S*>(stb);
+
+    F2 f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = fnext[i];
+    const uint32_t flag = flag_next;
+
+    // psi of node row k for both columns, then the halo columns.
+    T* ring_row = ring + (k % Sh::RING_H) * Sh::RING_W;
+    {
+      F2 rho;
+      static_for<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const F2 v = load_pair(st, ic);
+        fnext[i] = v;
+        rho = (i == 0) ? v : rho + v;
+      });
+      const T pa = pseudo_potential<Q, T>(a.phys, rho.x());
+      const T pb = pseudo_potential<Q, T>(a.phys, rho.y());
+      *reinterpret_cast<float2*>(ring_row + RO + xa) = make_float2(pa, pb);
+      flag_next = wall_on ? reinterpret_cast<const uint32_t*>(stb + Sh::NBOX * Sh::BOXSLOT)[tid >> 4]
+                          : 0u;
+    }
+    {
+      const int lane = tid & 31;
+      if (warp < 2 && lane < R) {
+        const int xl = warp == 0 ? lane - R : W + lane;
+        ring_row[xl + RO] = psi_at(st, xl);
+      }
+    }
+    __syncthreads();
+    if (*s_abort) break;
+
+    if (tid == kIss) {
+      const int fr = k - 1;
+      if (fr >= 0 && fr + NS < K) {
+        issue(fr + NS);
+        issued = fr + NS + 1;
+      }
+    }
+
+    if (k >= 2 * R) {
+      const int ko = k - R;
+      const int yo = y0 - R + ko;
+      // rho and j of both nodes, table order.
+      F2 rho = f[0], jx = f[1] - f[3], jy = f[2] - f[4];
+      {
+        rho += f[1];
+        rho += f[2];
+        rho += f[3];
+        rho += f[4];
+        rho += f[5];
+        rho += f[6];
+        rho += f[7];
+        rho += f[8];
+        jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+        jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+      }
+      const F2 inv_rho(T(1) / rho.x(), T(1) / rho.y());
+      const F2 ux = jx * inv_rho;
+      const F2 uy = jy * inv_rho;
+
+      // Neighbour psi: three aligned pairs per ring row cover columns xa-2 .. xa+3.
+      F2 sfx = F2::splat(0.f), sfy = F2::splat(0.f), psi_c;
+      static_for<0, 3>([&](auto rc) {
+        constexpr int cy = decltype(rc)::value - 1;
+        const T* row = ring + ((ko + cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa;
+        const float2 A = *reinterpret_cast<const float2*>(row - 2);
+        const float2 B = *reinterpret_cast<const float2*>(row);
+        const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
+        const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
+        if constexpr (cy == 0) {
+          psi_c = p0;
+          const F2 d = pp - pm;                       // (1,0) and (-1,0)
+          sfx = fma2(F2::splat(T(L::w(1))), d, sfx);
+        } else {
+          // (0,cy): weight w_axis; (+-1, cy): weight w_diag
+          const F2 axis = p0 * F2::splat(T(L::w(2)));
+          const F2 dsum = (pp + pm) * F2::splat(T(L::w(5)));
+          const F2 ddif = (pp - pm) * F2::splat(T(L::w(5)));
+          if constexpr (cy > 0) {
+            sfy = sfy + axis + dsum;
+          } else {
+            sfy = sfy - axis - dsum;
+          }
+          sfx = sfx + ddif;
+        }
+      });
+
+      // Force: F_FF, then the wall terms on flagged chunks, then body force.
+      const F2 mg = F2::splat(-a.phys.G) * psi_c;
+      const F2 ffx = mg * sfx, ffy = mg * sfy;
+      F2 Fx = ffx, Fy = ffy;
+      if (flag != 0u) {
+        T phe[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0}, wx[2] = {0, 0}, wy[2] = {0, 0};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (x + e < a.nx) {
+            const int64_t n = (int64_t)yo * a.nx + x + e;
+            phe[e] = a.wall.phie[n];
+            Sx[e] = a.wall.sx[n];
+            Sy[e] = a.wall.sy[n];
+            if (a.wall.uwx) {
+              wx[e] = a.wall.uwx[n];
+              wy[e] = a.wall.uwy[n];
+            }
+          }
+        }
+        const F2 rp = rho * F2(phe[0], phe[1]);
+        const F2 dfx = rp * (F2(wx[0], wx[1]) - ux - ffx * inv_rho);
+        const F2 dfy = rp * (F2(wy[0], wy[1]) - uy - ffy * inv_rho);
+        Fx = (ffx + rho * F2(Sx[0], Sx[1])) + dfx;
+        Fy = (ffy + rho * F2(Sy[0], Sy[1])) + dfy;
+      }
+      Fx += F2::splat(a.phys.bfx);
+      Fy += F2::splat(a.phys.bfy);
+
+      if (x < a.nx) {
+        if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
+          atomicOr(a.status, kStatusNonFinite);
+        if constexpr (MODE == kModeStep) {
+          const F2 usx = fma2(Fx, inv_rho, ux);
+          const F2 usy = fma2(Fy, inv_rho, uy);
+          // EDM-BGK in pair form (see node_collide), packed over the two nodes.
+          const F2 gg = F2::splat(a.phys.one_m_omega);
+          const F2 ax = usx - gg * ux, ay = usy - gg * uy;
+          const F2 Bt = (usx * usx + usy * usy - gg * (ux * ux + uy * uy)) *
+                        F2::splat(T(E::inv_2theta));
+          const F2 wB = F2::splat(a.phys.omega) - Bt;
+          if (a.phys.project) {
+            // rare path: per node
+            T fa[Q], fb[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              fa[i] = f[i].x();
+              fb[i] = f[i].y();
+            }
+            project<Q, T>(fa, rho.x(), jx.x(), jy.x());
+            project<Q, T>(fb, rho.y(), jx.y(), jy.y());
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = F2(fa[i], fb[i]);
+          }
+          static_for<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int j = opposite<Q>(i);
+            if constexpr (i == L::REST) {
+              f[i] = fma2(gg, f[i], F2::splat(T(L::w(i))) * rho * wB);
+            } else if constexpr (i < j) {
+              const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
+              const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
+              const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax, ay);
+              const F2 wr = F2::splat(T(L::w(i))) * rho;
+              const F2 t = cs * cs - gg * (cu * cu);
+              const F2 Sp = wr * fma2(t, F2::splat(T(E::inv_2theta2)), wB);
+              const F2 Ap = wr * (ca * F2::splat(T(E::inv_theta)));
+              const F2 fi = fma2(gg, f[i], Sp + Ap);
+              const F2 fj = fma2(gg, f[j], Sp - Ap);
+              f[i] = fi;
+              f[j] = fj;
+            }
+          });
+          {  // mass closure of the rest population (FP32 arithmetic)
+            F2 moving = f[1];
+            moving += f[2];
+            moving += f[3];
+            moving += f[4];
+            moving += f[5];
+            moving += f[6];
+            moving += f[7];
+            moving += f[8];
+            f[0] = rho - moving;
+          }
+          S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
+          if (pair_ok) {
+            static_for<0, Q>([&](auto ic) {
+              constexpr int i = decltype(ic)::value;
+              *reinterpret_cast<typename PR::Raw*>(out + Planes<Q>::template plane<i> * a.plane) =
+                  PR::enc(f[i], F2::splat(T(L::w(i)) * rho_s));
+            });
+          } else {
+            static_for<0, Q>([&](auto ic) {
+              constexpr int i = decltype(ic)::value;
+              out[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i].x(), T(L::w(i)) * rho_s);
+            });
+          }
+          const bool edge = (strip_edge && (x < GX || x + 1 >= a.nx - GX)) || yo < GY ||
+                            yo >= a.ny - GY;
+          if (edge) {
+#pragma unroll 1
+            for (int e = 0; e < 2; ++e) {
+              const int xn = x + e;
+              if (xn >= a.nx) break;
+              int xs = xn;
+              while (xs - a.nx >= -GX) xs -= a.nx;
+              int ya = yo;
+              while (ya - a.ny >= -GY) ya -= a.ny;
+              for (int ym = ya; ym < a.ny + GY; ym += a.ny) {
+                for (int xm = xs; xm < a.nx + GX; xm += a.nx) {
+                  if (xm == xn && ym == yo) continue;
+                  S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
+                  static_for<0, Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    const T v = e == 0 ? f[i].x() : f[i].y();
+                    o2[Planes<Q>::template plane<i> * a.plane] = C::enc(v, T(L::w(i)) * rho_s);
+                  });
+                }
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            if (x + e >= a.nx) break;
+            const int64_t n = (int64_t)yo * a.nx + x + e;
+            const double r = e == 0 ? rho.x() : rho.y();
+            const double px = (double)(e == 0 ? jx.x() : jx.y()) + 0.5 * (double)(e == 0 ? Fx.x() : Fx.y());
+            const double py = (double)(e == 0 ? jy.x() : jy.y()) + 0.5 * (double)(e == 0 ? Fy.x() : Fy.y());
+            a.out_rho[n] = r;
+            if (a.momentum) {
+              a.out_ux[n] = px;
+              a.out_uy[n] = py;
+            } else {
+              a.out_ux[n] = px / r;
+              a.out_uy[n] = py / r;
+            }
+          }
+        }
+      }
+    }
+    if (++s == NS) {
+      s = 0;
+      phase ^= 1u;
+    }
+  }
+
+  g = g0 + (uint32_t)K;
+  if (*s_abort) {
+    if (tid == kIss) {
+      atomicOr(a.status, kStatusTimeout);
+      for (int r = k; r < issued; ++r) {
+        const uint32_t gr = g0 + (uint32_t)r;
+        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u);
+      }
+    }
+    return false;
+  }
+  return true;
+}
+
+// Marches one segment with the variant the shape selects (one or two nodes
+// per thread).
+template <int Q, typename S, int W, int NS, int MODE, typename Args>
+__device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensorMap* flg,
+                                          const Args& a, int x0, int y0, int Lr,
+                                          const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
+                                          uint64_t policy) {
+  if constexpr (StepShape<Q, S, W, NS>::V == 2)
+    return march_segment_v2<S, W, NS, MODE>(src, flg, a, x0, y0, Lr, sm, g);
+  else
+    return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, sm, g, policy);
+}
+
 // One time step of one lattice: CTA (bx, by) marches strip bx, segment by.
 template <int Q, typename S, int W, int NS, int MODE, int MINB>
-__global__ void __launch_bounds__(W, MINB)
+__global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
                 const StepArgs<typename Codec<S>::T, S> a) {
   extern __shared__ unsigned char smem_raw[];
@@ -398,8 +773,8 @@ __global__ void __launch_bounds__(W, MINB)
   const uint64_t policy = step_smem_init(sm);
   const int y0 = blockIdx.y * a.tile_rows;
   uint32_t g = 0;
-  march_segment<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
-                                   sm, g, policy);
+  march_any<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
+                               sm, g, policy);
 }
 
 // A lattice of a batch: TMA maps of its two population buffers and of its wall
@@ -421,7 +796,7 @@ struct BatchTile {
 // [first[b], first[b + 1]) in order; `parity` flips the read/write buffers on
 // alternate steps.
 template <int Q, typename S, int W, int NS, int MINB>
-__global__ void __launch_bounds__(W, MINB)
+__global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     batch_step_kernel(const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
                       const BatchTile* __restrict__ tiles, const int32_t* __restrict__ first,
                       int32_t parity) {
@@ -440,8 +815,8 @@ __global__ void __launch_bounds__(W, MINB)
     __syncthreads();  // the previous tile no longer reads s_args
     if (threadIdx.x == 0) s_args = m->args[dir];
     __syncthreads();
-    if (!march_segment<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
-                                              tile.rows, sm, g, policy))
+    if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
+                                          tile.rows, sm, g, policy))
       return;
   }
 }

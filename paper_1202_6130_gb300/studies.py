@@ -1,0 +1,228 @@
+"""Measurement studies on the GPU engine (host-side drivers; every time step
+runs in the fused kernel, several lattices at once through a Batch).
+
+  contact_angle_sweep  static contact angle of a 1024x512 drop (R = 160) for 8
+                       tail strengths G_A in [0, 0.1] at G_R = 0.1, per storage
+                       precision, with convergence history and spurious currents
+  slip_study           slip length of a body-force-driven liquid channel, per
+                       storage precision (x-invariant: a narrow periodic slice)
+  large_precision      mass drift and density error of the 8192x4096 lattice in
+                       FP32 / FP16S / BF16S storage against FP64 storage
+  paper_theta_table    the paper's fluid (D2Q21, Eq. EOS, projection) with
+                       Appendix wall functions: static angle vs G_A at G_R = 1.33,
+                       next to the angles printed in Sec. III B
+
+  python -m paper_1202_6130_gb300.studies sweep|slip|large|paper [--steps N] ...
+prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import analysis
+from .sim import Batch, Simulation, wall_gaussian_filter
+
+STORAGES = ("fp64", "fp32", "fp16s", "bf16s")
+
+
+def _run_batch(sims, steps: int, chunk: int, on_chunk=None):
+    b = Batch()
+    for s in sims:
+        b.add(s)
+    done = 0
+    while done < steps:
+        n = min(chunk, steps - done)
+        b.step(n)
+        done += n
+        if on_chunk is not None:
+            b.synchronize()
+            on_chunk(done)
+    b.synchronize()
+    b.close()
+
+
+def contact_angle_sweep(storages=STORAGES, steps: int = 50000, chunk: int = 10000,
+                        n_tail: int = 8, nx: int = 1024, ny: int = 512, R: float = 160.0,
+                        G_R: float = 0.1, G_A_max: float = 0.1):
+    import workloads as W
+    gas = [G_A_max * k / (n_tail - 1) for k in range(n_tail)]
+    out = {"nx": nx, "ny": ny, "R": R, "G_R": G_R, "G_A": gas, "steps": steps, "storages": {}}
+    for st in storages:
+        ws = [W.droplet_on_wall(nx=nx, ny=ny, R=R, G_A=ga, G_R=G_R, noise_amp=1e-6, seed=0)
+              for ga in gas]
+        sims = [Simulation.from_workload(w, storage=st) for w in ws]
+        m0 = [s.totals()[0] for s in sims]
+        hist = {i: [] for i in range(len(sims))}
+
+        def record(done):
+            for i, (s, w) in enumerate(zip(sims, ws)):
+                rho, ux, uy = s.moments()
+                try:
+                    th = analysis.contact_angle(rho, w.phi_s, w.meta["rho_l"], w.meta["rho_v"]).theta_deg
+                except Exception:
+                    th = float("nan")
+                hist[i].append((done, th, analysis.spurious_current(ux, uy)))
+
+        t0 = time.perf_counter()
+        _run_batch(sims, steps, chunk, record)
+        wall = time.perf_counter() - t0
+        m1 = [s.totals()[0] for s in sims]
+        out["storages"][st] = {
+            "theta_deg": [h[-1][1] for h in hist.values()],
+            "theta_change_last_chunk_deg": [h[-1][1] - h[-2][1] if len(h) > 1 else float("nan")
+                                            for h in hist.values()],
+            "spurious_current": [h[-1][2] for h in hist.values()],
+            "mass_drift_rel": [(b - a) / a for a, b in zip(m0, m1)],
+            "history": {str(gas[i]): h for i, h in hist.items()},
+            "wall_s": wall}
+        for s in sims:
+            s.close()
+    if "fp64" in out["storages"]:
+        ref = np.array(out["storages"]["fp64"]["theta_deg"])
+        for st, d in out["storages"].items():
+            d["theta_err_vs_fp64_deg"] = list(np.array(d["theta_deg"]) - ref)
+    return out
+
+
+def slip_study(storages=STORAGES, nx: int = 8, ny: int = 256, steps: int = 300000,
+               chunk: int = 50000, force: float = 1e-6, epsilons=(1.0, 1.3)):
+    import workloads as W
+    out = {"nx": nx, "ny": ny, "force": force, "steps": steps, "storages": {}}
+    for st in storages:
+        res = {}
+        for eps in epsilons:
+            w = W.poiseuille_channel(nx=nx, ny=ny, force=force, epsilon=eps)
+            sim = Simulation.from_workload(w, storage=st)
+            hist = []
+
+            def record(done):
+                _, ux, _ = sim.moments()
+                hist.append((done, analysis.slip_length(ux, w.phi_s).slip_length,
+                             float(ux.max())))
+
+            _run_batch([sim], steps, chunk, record)
+            rho, ux, uy = sim.moments()
+            s = analysis.slip_length(ux, w.phi_s)
+            res[str(eps)] = {"slip_length": s.slip_length, "y_w": s.y_w, "u_max": float(ux.max()),
+                             "curvature": s.curvature,
+                             "curvature_expected": -force / (float(rho[ny // 2].mean()) * (1.0 / 3.0) * 0.5),
+                             "history": hist}
+            sim.close()
+        out["storages"][st] = res
+    if "fp64" in out["storages"]:
+        for st, d in out["storages"].items():
+            for eps, r in d.items():
+                ref = out["storages"]["fp64"][eps]["slip_length"]
+                r["slip_rel_err_vs_fp64"] = (r["slip_length"] - ref) / ref if ref else float("nan")
+    return out
+
+
+def large_precision(storages=("fp32", "fp16s", "bf16s"), steps: int = 20000):
+    """8192x4096 multi-drop lattice: each storage precision against FP64 storage
+    after `steps` steps (mass drift, density differences)."""
+    import workloads as W
+    w = W.large_multi_droplet(noise_amp=0.0)
+    ref = Simulation.from_workload(w, storage="fp64")
+    m0 = ref.totals()[0]
+    t0 = time.perf_counter()
+    ref.step(steps)
+    rho64 = ref.moments()[0]
+    t64 = time.perf_counter() - t0
+    out = {"steps": steps, "fp64": {"mass_drift_rel": (ref.totals()[0] - m0) / m0, "wall_s": t64}}
+    ref.close()
+    for st in storages:
+        sim = Simulation.from_workload(w, storage=st)
+        a = sim.totals()[0]
+        sim.step(steps)
+        rho = sim.moments()[0]
+        b = sim.totals()[0]
+        d = np.abs(rho - rho64)
+        out[st] = {"mass_drift_rel": (b - a) / a, "mass_vs_fp64_rel": (b - m0) / m0,
+                   "rho_max_abs_err": float(d.max()), "rho_mean_abs_err": float(d.mean()),
+                   "rho_rms_err": float(np.sqrt((d * d).mean())),
+                   "finite": bool(np.isfinite(rho).all())}
+        sim.close()
+    return out
+
+
+# Angles printed in Sec. III B (Figs. 6-7 captions): G_R = 1.33, R0 = 50, 650 x 150.
+PAPER_THETA = {0.0: 150.0, 0.2: 112.0, 0.5: 58.7, 0.7: 36.7, 0.8: 30.9, 0.9: 24.0}
+
+
+def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
+                      nx: int = 650, ny: int = 150, R0: float = 50.0, G_R: float = 1.33,
+                      tau: float = 1.0, solid_rows: int = 1):
+    """The paper's fluid and walls: D2Q21, Eq. EOS (theta_V = theta/4, theta_U =
+    -theta/4, theta_L = theta, rho_1 = 0.222, rho_2 = 0.869) with G = -1/theta,
+    projection on, wall functions from the Appendix filter of a solid slab
+    (psi_R = G^(5), psi_A = G^(22) - G^(5), phi_S = G^(22), epsilon = 1).  A
+    disc of area pi R0^2 starts tangent to the wall; the static angle is fitted
+    as for the other drops.  Readings (1/theta in the force, the sign of
+    psi_FS) are the ones the oracle uses."""
+    import workloads as W
+    th = 2.0 / 3.0
+    solid = np.zeros((ny, nx), bool)
+    solid[:solid_rows, :] = True
+    phi, pr, pa = wall_gaussian_filter(solid, lattice=21, n_rep=5, n_att=22)
+    yb = analysis.surface_line(phi[:, 0], 0.5)
+    rho_l, rho_v = 1.0, 0.1
+    sims, meta = [], []
+    for ga in PAPER_THETA:
+        rho = W.droplet_density(nx, ny, [(nx / 2.0, yb + R0)], [R0], rho_l, rho_v, 3.0)
+        s = Simulation(nx, ny, lattice=21, storage=storage, tau=tau, G=-1.0 / th, psi_kind=1,
+                       project=True, eos=(0.25 * th, -0.25 * th, th, 0.222, 0.869))
+        s.set_wall(phi, pr, pa, G_R, ga, 1.0)
+        s.set_equilibrium(rho)
+        sims.append(s)
+        meta.append(ga)
+    hist = {ga: [] for ga in meta}
+
+    def record(done):
+        for s, ga in zip(sims, meta):
+            rho, ux, uy = s.moments()
+            try:
+                c = analysis.contact_angle(rho, phi, rho_l, rho_v, y_max=ny - 10)
+                hist[ga].append((done, c.theta_deg, c.R))
+            except Exception:
+                hist[ga].append((done, float("nan"), float("nan")))
+
+    t0 = time.perf_counter()
+    _run_batch(sims, steps, chunk, record)
+    out = {"nx": nx, "ny": ny, "R0": R0, "G_R": G_R, "steps": steps, "storage": storage,
+           "wall_s": time.perf_counter() - t0, "y_surface": yb, "rows": []}
+    for s, ga in zip(sims, meta):
+        th_end = hist[ga][-1][1]
+        out["rows"].append({"G_A": ga, "theta_deg": th_end, "paper_theta_deg": PAPER_THETA[ga],
+                            "diff_deg": th_end - PAPER_THETA[ga],
+                            "theta_change_last_chunk_deg":
+                                th_end - hist[ga][-2][1] if len(hist[ga]) > 1 else float("nan"),
+                            "history": hist[ga]})
+        s.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["sweep", "slip", "large", "paper"])
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--storages", default=None, help="comma-separated storage modes")
+    args = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    kw = {}
+    if args.steps is not None:
+        kw["steps"] = args.steps
+    if args.storages and args.which != "paper":
+        kw["storages"] = tuple(args.storages.split(","))
+    fn = {"sweep": contact_angle_sweep, "slip": slip_study, "large": large_precision,
+          "paper": paper_theta_table}[args.which]
+    print(json.dumps(fn(**kw), default=float))
+
+
+if __name__ == "__main__":
+    main()

@@ -82,3 +82,33 @@ def test_core_tail_helper_matches_input_generator(lib):
     for u, v in zip(a, b):
         # 1 - tanh(.) cancels: compare absolutely at the FP64 rounding level
         np.testing.assert_allclose(u, v, rtol=1e-14, atol=1e-15)
+
+
+def test_allocator_failure_is_enomem(lib):
+    """Failure injected through the allocator callback: the first request (a
+    population buffer, made before the library touches a device) returns NULL;
+    lbm_create reports LBM_ENOMEM, returns no context and holds no block."""
+    fail_at = 1
+    from paper_1202_6130_gb300 import _lib
+    live, calls = set(), [0]
+
+    def alloc(n, user):
+        calls[0] += 1
+        if calls[0] >= fail_at:
+            return None
+        p = 0x1000 * calls[0]          # a fake address; never dereferenced
+        live.add(p)
+        return p
+
+    def free(p, user):
+        live.discard(p)
+
+    a = _lib.lbm_allocator(_lib.ALLOC_FN(alloc), _lib.FREE_FN(free), None)
+    p = _lib.lbm_params()
+    lib.lbm_params_default(ctypes.byref(p))
+    ctx = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(p), ctypes.byref(a), None, ctypes.byref(ctx))
+    assert rc == _lib.LBM_ENOMEM
+    assert not ctx.value
+    assert not live
+    assert b"population buffer" in lib.lbm_last_error(None)

@@ -313,3 +313,33 @@ def test_full_size_fp32_sampled_nodes_match_oracle(pkg):
         fg = f1[:, y, x]
         err = np.max(np.abs(fg - fo) / np.maximum(np.abs(fo), 1e-3))
         assert err < 1e-5, (y, x, err)
+
+
+def test_allocator_failure_midway_frees_what_was_obtained(pkg):
+    """Failure injected on the third device allocation (after both population
+    buffers were obtained from torch): LBM_ENOMEM, and every block handed out
+    is returned through the free callback."""
+    import ctypes
+    import torch
+    from paper_1202_6130_gb300 import _lib
+    lib = _lib.load()
+    live, calls = {}, [0]
+
+    def alloc(n, user):
+        calls[0] += 1
+        if calls[0] >= 3:
+            return None
+        t = torch.empty(int(n), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(p, user):
+        live.pop(p, None)
+
+    a = _lib.lbm_allocator(_lib.ALLOC_FN(alloc), _lib.FREE_FN(free), None)
+    p = _lib.lbm_params()
+    lib.lbm_params_default(ctypes.byref(p))
+    ctx = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(p), ctypes.byref(a), None, ctypes.byref(ctx))
+    assert rc == _lib.LBM_ENOMEM and not ctx.value
+    assert not live and calls[0] >= 3
