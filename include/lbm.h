@@ -164,6 +164,15 @@ int lbm_destroy(lbm_ctx* c);
  * lbm_last_error(NULL) reports errors of calls that had no context yet. */
 const char* lbm_last_error(const lbm_ctx* c);
 
+/* Test hook for failure detection: arms the next lbm_step so that every
+ * shared-memory stage of its kernel expects 16 bytes more than its copies
+ * deliver.  The stage waits then run out after wait_ms milliseconds (instead
+ * of the normal 2 s bound), the kernel records a timeout in the context's
+ * status word and returns, and lbm_sync (or a periodic check) reports
+ * LBM_ETIMEOUT.  Nothing faults and the context stays usable; the populations
+ * of that step are not valid, so set them again.  Covers one step. */
+int lbm_debug_stall_next_step(lbm_ctx* c, int32_t wait_ms);
+
 /* Layout facts for measurement: bytes per node per step that the population
  * traffic needs (2 Q s), the padded row pitch in elements, and the launch shape
  * (strip width, rows per CTA, grid) of the fused step. */

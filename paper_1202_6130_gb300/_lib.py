@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_destroy": (c_int, [c_void_p]),
     "lbm_last_error": (c_char_p, [c_void_p]),
     "lbm_get_layout": (c_int, [c_void_p, POINTER(lbm_layout)]),
+    "lbm_debug_stall_next_step": (c_int, [c_void_p, c_int32]),
     "lbm_wall_gaussian_filter": (c_int, [c_int32, c_int32, c_int32, POINTER(c_uint8), c_int32,
                                          c_int32, _DP, _DP, _DP]),
     "lbm_wall_core_tail": (c_int, [c_int32, c_int32, _DP, _DP, c_double, c_double, c_double,

@@ -52,6 +52,8 @@ struct lbm_ctx {
   double rho_s = 0.0;
   int tile_rows = 0, grid_x = 0, grid_y = 0;
   uint64_t version = 0;  // bumped whenever device pointers or parameters change
+  uint64_t wait_ns = 2000000000ull;  // bound of every stage wait in the step kernels
+  uint64_t stall_wait_ns = 0;        // test hook: armed stall for the next step
 };
 
 namespace {
@@ -279,6 +281,8 @@ StepArgs<typename Codec<S>::T, S> make_args(const lbm_ctx* c, S* fout, double* o
   a.out_uy = o_uy;
   a.momentum = momentum;
   a.status = c->d_status;
+  a.wait_ns = c->stall_wait_ns ? c->stall_wait_ns : c->wait_ns;
+  a.extra_tx = c->stall_wait_ns ? 16u : 0u;
   return a;
 }
 
@@ -557,6 +561,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
                             static_cast<S*>(c->buf[c->cur ^ 1]));
     });
     if (rc) return rc;
+    c->stall_wait_ns = 0;  // the test hook covers one step
     c->cur ^= 1;
     c->steps += 1;
     if (c->p.check_every > 0 && c->steps % c->p.check_every == 0) {
@@ -663,6 +668,14 @@ int lbm_destroy(lbm_ctx* c) {
 }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+int lbm_debug_stall_next_step(lbm_ctx* c, int32_t wait_ms) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (wait_ms < 1) return fail(c, LBM_EINVAL, "wait_ms must be >= 1");
+  c->stall_wait_ns = (uint64_t)wait_ms * 1000000ull;
+  return LBM_OK;
+}
 
 int lbm_get_layout(const lbm_ctx* c, lbm_layout* out) {
   if (!c || !out) return fail(nullptr, LBM_EINVAL, "null argument");

@@ -54,6 +54,8 @@ template <typename T, typename S> struct StepArgs {
   double* out_uy;
   int32_t momentum;    // kModeMoments: 1 -> out_ux/out_uy get j + F/2 instead of u
   uint32_t* status;    // error bits (kStatus*)
+  uint64_t wait_ns;    // bound of every stage wait
+  uint32_t extra_tx;   // test hook: bytes each stage expects beyond its copies (0 normally)
 };
 
 template <int Q, typename S, int W, int NS> struct StepShape {
@@ -179,7 +181,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
-  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
+  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
 
   // Every thread is done with the stages and ring of the previous segment.
@@ -242,7 +244,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   // (kRegs) alternate between register sets instead of being copied.
 #pragma unroll 2
   for (; k < K; ++k) {
-    if (!mbar_wait_bounded(&bars[s], phase)) *s_abort = 1;
+    if (!mbar_wait_bounded(&bars[s], phase, a.wait_ns)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
     // Populations of the row collided in this iteration (row k - R).
@@ -395,7 +397,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       atomicOr(a.status, kStatusTimeout);
       for (int r = k; r < issued; ++r) {
         const uint32_t gr = g0 + (uint32_t)r;
-        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u);
+        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u, a.wait_ns);
       }
     }
     return false;
@@ -440,7 +442,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const bool pair_ok = x + 1 < a.nx;  // both nodes exist
-  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u);
+  const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
 
   __syncthreads();
@@ -499,7 +501,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   int k = 0;
 #pragma unroll 2
   for (; k < K; ++k) {
-    if (!mbar_wait_bounded(&bars[s], phase)) *s_abort = 1;
+    if (!mbar_wait_bounded(&bars[s], phase, a.wait_ns)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
 
@@ -742,7 +744,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
       atomicOr(a.status, kStatusTimeout);
       for (int r = k; r < issued; ++r) {
         const uint32_t gr = g0 + (uint32_t)r;
-        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u);
+        mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u, a.wait_ns);
       }
     }
     return false;

@@ -1,7 +1,7 @@
 // Thin inline-PTX wrappers for the sm_100-family asynchronous copy path:
 // mbarrier transaction barriers and tiled TMA (cp.async.bulk.tensor) loads.
-// Every wait is bounded: it gives up after a fixed number of try_wait rounds
-// so a lost transaction turns into an error status instead of a hang.
+// Every wait is bounded in time, so a transaction that never completes turns
+// into an error status instead of a hang.
 #pragma once
 
 #include <cstdint>
@@ -43,16 +43,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on phase `parity`.  try_wait itself suspends for a hardware
-// dependent interval, so the bound below is well above any legitimate wait
-// (a TMA row lands in microseconds) and far below a watchdog timeout.
-constexpr uint32_t kWaitRounds = 1u << 22;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitRounds; ++it) {
+// Bounded wait on phase `parity`: gives up after `limit_ns` nanoseconds (a
+// TMA row normally lands within microseconds).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {

@@ -343,3 +343,27 @@ def test_allocator_failure_midway_frees_what_was_obtained(pkg):
     rc = lib.lbm_create(ctypes.byref(p), ctypes.byref(a), None, ctypes.byref(ctx))
     assert rc == _lib.LBM_ENOMEM and not ctx.value
     assert not live and calls[0] >= 3
+
+
+def test_stage_wait_runs_out_and_reports_timeout(pkg):
+    """Failure detection without a fault: the test hook makes every stage of
+    the next step expect more bytes than its copies bring, so each bounded
+    wait runs out (after 20 ms here); the step reports LBM_ETIMEOUT through the
+    status word, and the context keeps working once its populations are set
+    again."""
+    from paper_1202_6130_gb300 import _lib
+    lib = _lib.load()
+    w = _small_case(96, 40)
+    sim = make_sim(pkg, w, "fp32")
+    sim.step(2)
+    assert lib.lbm_debug_stall_next_step(sim.ctx, 20) == 0
+    sim.step(1)                               # enqueued; the waits expire on the GPU
+    with pytest.raises(pkg.LbmError) as ei:
+        sim.sync()
+    assert "ETIMEOUT" in str(ei.value)
+    sim.set_equilibrium(w.rho, w.ux, w.uy, w.noise)
+    sim.step(5)
+    sim.sync()
+    ref = make_sim(pkg, w, "fp32")
+    ref.step(5)
+    np.testing.assert_array_equal(sim.populations(), ref.populations())
