@@ -160,3 +160,66 @@ def laplace_jump(rho: np.ndarray, G: float, center, r_in: float, r_out: float,
 def spurious_current(ux: np.ndarray, uy: np.ndarray) -> float:
     """max |u| over the lattice."""
     return float(np.sqrt(ux * ux + uy * uy).max())
+
+
+def recenter_x(rho: np.ndarray, rho_mid: float):
+    """Rolls a periodic field in x so that the liquid's circular-mean column is
+    at nx/2 (a moving drop may straddle the periodic seam).  Returns the
+    shift applied (columns) so that other fields can be rolled the same way."""
+    ny, nx = rho.shape
+    w = np.clip(rho - rho_mid, 0.0, None).sum(axis=0)
+    ang = 2.0 * np.pi * np.arange(nx) / nx
+    c = math.atan2(float((w * np.sin(ang)).sum()), float((w * np.cos(ang)).sum()))
+    xc = (c / (2.0 * np.pi) * nx) % nx
+    return int(round(nx / 2.0 - xc))
+
+
+@dataclass
+class DynamicAngles:
+    theta_adv_deg: float
+    theta_rec_deg: float
+    x_apex: float
+    h: float
+    front: tuple
+    rear: tuple
+    npoints: tuple
+
+
+def dynamic_angles(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
+                   y_max=None, direction: int = 1) -> DynamicAngles:
+    """Advancing and receding angles of a drop moving along +x (direction=1):
+    the interface contour rho = (rho_l + rho_v)/2 in the hydrodynamic region is
+    split at the apex; one circle is fitted to the points ahead of it (front)
+    and one to those behind it (rear), and each angle is acos((y_b - y_c)/R)
+    with y_b the solid surface phi_S = 0.5 (Sec. III C)."""
+    ny, nx = rho.shape
+    shift = recenter_x(rho, 0.5 * (rho_l + rho_v))
+    rho = np.roll(rho, shift, axis=1)
+    phi_s = np.roll(phi_s, shift, axis=1)
+    y_max = ny // 2 if y_max is None else y_max
+    mask = phi_s < 0.01
+    mask[y_max:, :] = False
+    x, y = contour_points(rho, 0.5 * (rho_l + rho_v), mask)
+    if len(x) < 10:
+        raise ValueError("too few interface points")
+    ia = int(np.argmax(y))
+    xa = float(x[ia])
+    front = (x - xa) * direction >= 0
+    rear = ~front
+    yb = surface_line(phi_s[:, nx // 2], 0.5)
+    out = []
+    for sel in (front, rear):
+        xc, yc, R = fit_circle(x[sel], y[sel])
+        c = max(-1.0, min(1.0, (yb - yc) / R))
+        out.append((math.degrees(math.acos(c)), (xc - shift) % nx, yc, R))
+    return DynamicAngles(out[0][0], out[1][0], (xa - shift) % nx, float(y[ia] - yb),
+                         out[0][1:], out[1][1:], (int(front.sum()), int(rear.sum())))
+
+
+def drop_velocity(rho: np.ndarray, ux: np.ndarray, rho_mid: float, phi_s=None) -> float:
+    """Mass-weighted mean x velocity of the liquid (rho > rho_mid), outside the
+    solid (phi_S < 0.5) when phi_S is given."""
+    m = rho > rho_mid
+    if phi_s is not None:
+        m &= phi_s < 0.5
+    return float((rho[m] * ux[m]).sum() / rho[m].sum())

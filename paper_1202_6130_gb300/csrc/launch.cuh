@@ -13,11 +13,13 @@ namespace lbm {
 // CTA width, TMA pipeline depth and the CTAs per SM the register budget is
 // sized for, per (lattice, storage).  Shared memory per CTA is
 // NS * (Q box slots + flag slot) + the psi ring.
+// (D2Q9 FP32 and 16-bit values measured on GB300: NS 4 / MINB 8 for FP32 and
+// MINB 10 for 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12.)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
-  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 5 : 6))
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6))
                                      : (sizeof(S) == 8 ? 5 : 6);
-  static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 6 : 8))
+  static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
                                        : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3));
 };
 

@@ -11,8 +11,11 @@ runs in the fused kernel, several lattices at once through a Batch).
   paper_theta_table    the paper's fluid (D2Q21, Eq. EOS, projection) with
                        Appendix wall functions: static angle vs G_A at G_R = 1.33,
                        next to the angles printed in Sec. III B
+  dynamic_angles       the same drop driven along the wall by a uniform force:
+                       droplet speed, capillary number, advancing and receding
+                       angles (Sec. III C)
 
-  python -m paper_1202_6130_gb300.studies sweep|slip|large|paper [--steps N] ...
+  python -m paper_1202_6130_gb300.studies sweep|slip|large|paper|dynamic [--steps N] ...
 prints one JSON object.
 """
 from __future__ import annotations
@@ -206,9 +209,87 @@ def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "f
     return out
 
 
+def _paper_sim(nx, ny, storage, tau, G_R, G_A, eps, phi, pr, pa, body=(0.0, 0.0)):
+    th = 2.0 / 3.0
+    s = Simulation(nx, ny, lattice=21, storage=storage, tau=tau, G=-1.0 / th, psi_kind=1,
+                   project=True, eos=(0.25 * th, -0.25 * th, th, 0.222, 0.869), body_force=body)
+    s.set_wall(phi, pr, pa, G_R, G_A, eps)
+    return s
+
+
+def dynamic_angles(steps_static: int = 60000, steps: int = 100000, chunk: int = 25000,
+                   dps=(0.175e-4, 1.75e-4, 3.5e-4, 5.25e-4),
+                   surfaces=((1.33, 0.5, 1.0), (0.9, 0.42, 1.0), (1.33, 0.57, 1.3)),
+                   storage: str = "fp32", nx: int = 650, ny: int = 150, R0: float = 50.0,
+                   tau: float = 1.0, gamma: float = 0.09):
+    """Contact-angle dynamics of Sec. III C: each surface (G_R, G_A, epsilon)
+    first relaxes a static drop; the relaxed populations then restart under a
+    uniform force density dp / nx along +x (a pressure difference dp over the
+    domain length).  Reported per run: droplet speed U (mass-weighted liquid
+    velocity), Ca = U mu_L / gamma with mu_L = rho_L theta (tau - 1/2) and the
+    paper's gamma = 0.09, and the advancing / receding angles from two circle
+    fits, with their change over the last chunk."""
+    import workloads as W
+    th = 2.0 / 3.0
+    solid = np.zeros((ny, nx), bool)
+    solid[0, :] = True
+    phi, pr, pa = wall_gaussian_filter(solid, lattice=21, n_rep=5, n_att=22)
+    yb = analysis.surface_line(phi[:, 0], 0.5)
+    rho_l, rho_v = 1.0, 0.1
+    mu_l = rho_l * th * (tau - 0.5)
+    out = {"nx": nx, "ny": ny, "R0": R0, "tau": tau, "gamma": gamma, "storage": storage,
+           "steps_static": steps_static, "steps": steps, "runs": []}
+    statics = []
+    for (GR, GA, eps) in surfaces:
+        s = _paper_sim(nx, ny, storage, tau, GR, GA, eps, phi, pr, pa)
+        s.set_equilibrium(W.droplet_density(nx, ny, [(nx / 2.0, yb + R0)], [R0], rho_l, rho_v, 3.0))
+        statics.append(s)
+    _run_batch(statics, steps_static, steps_static)
+    f0s = []
+    for s, (GR, GA, eps) in zip(statics, surfaces):
+        rho, _, _ = s.moments()
+        c = analysis.contact_angle(rho, phi, rho_l, rho_v, y_max=ny - 10)
+        f0s.append(s.populations())
+        out["runs"].append({"G_R": GR, "G_A": GA, "epsilon": eps, "dp": 0.0,
+                            "theta_static_deg": c.theta_deg})
+        s.close()
+    sims, meta = [], []
+    for f0, (GR, GA, eps) in zip(f0s, surfaces):
+        for dp in dps:
+            s = _paper_sim(nx, ny, storage, tau, GR, GA, eps, phi, pr, pa, body=(dp / nx, 0.0))
+            s.set_populations(f0)
+            sims.append(s)
+            meta.append((GR, GA, eps, dp))
+    hist = {i: [] for i in range(len(sims))}
+
+    def record(done):
+        for i, s in enumerate(sims):
+            rho, ux, uy = s.moments()
+            try:
+                d = analysis.dynamic_angles(rho, phi, rho_l, rho_v, y_max=ny - 10)
+                U = analysis.drop_velocity(rho, ux, 0.5 * (rho_l + rho_v), phi)
+                hist[i].append((done, d.theta_adv_deg, d.theta_rec_deg, U))
+            except Exception:
+                hist[i].append((done, float("nan"), float("nan"), float("nan")))
+
+    t0 = time.perf_counter()
+    _run_batch(sims, steps, chunk, record)
+    for i, (GR, GA, eps, dp) in enumerate(meta):
+        h = hist[i]
+        last, prev = h[-1], h[-2] if len(h) > 1 else h[-1]
+        out["runs"].append({"G_R": GR, "G_A": GA, "epsilon": eps, "dp": dp, "U": last[3],
+                            "Ca": last[3] * mu_l / gamma, "theta_adv_deg": last[1],
+                            "theta_rec_deg": last[2],
+                            "theta_adv_change_last_chunk": last[1] - prev[1],
+                            "theta_rec_change_last_chunk": last[2] - prev[2], "history": h})
+        sims[i].close()
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["sweep", "slip", "large", "paper"])
+    ap.add_argument("which", choices=["sweep", "slip", "large", "paper", "dynamic"])
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--storages", default=None, help="comma-separated storage modes")
     args = ap.parse_args(argv)
@@ -217,10 +298,10 @@ def main(argv=None):
     kw = {}
     if args.steps is not None:
         kw["steps"] = args.steps
-    if args.storages and args.which != "paper":
+    if args.storages and args.which not in ("paper", "dynamic"):
         kw["storages"] = tuple(args.storages.split(","))
     fn = {"sweep": contact_angle_sweep, "slip": slip_study, "large": large_precision,
-          "paper": paper_theta_table}[args.which]
+          "paper": paper_theta_table, "dynamic": dynamic_angles}[args.which]
     print(json.dumps(fn(**kw), default=float))
 
 

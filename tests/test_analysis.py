@@ -43,3 +43,28 @@ def test_slip_length_of_a_shifted_parabola():
 def test_laplace_pressure_of_a_flat_state_is_zero():
     rho = np.full((64, 64), 1.3)
     assert abs(A.laplace_jump(rho, -5.5, (32, 32), 5, 20)) < 1e-15
+
+
+def test_dynamic_angles_of_two_joined_circular_arcs():
+    """A drop whose front is an arc of 70 deg and whose rear is an arc of 50
+    deg (same apex height): the two-circle fit returns both angles, also when
+    the drop straddles the periodic seam."""
+    nx, ny = 600, 200
+    dist = W.wall_distance_slab(nx, ny)
+    phi, _, _ = W.wall_core_tail(dist, 3.0)
+    yb = A.surface_line(phi[:, 0], 0.5)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    h = 40.0
+    dens = np.full((ny, nx), 0.1)
+    for th_deg, side in ((70.0, 1), (50.0, -1)):
+        th = math.radians(th_deg)
+        R = h / (1.0 - math.cos(th))
+        yc = yb + h - R
+        xa = 300.0
+        r = np.sqrt((x - xa) ** 2 + (y - yc) ** 2)
+        cap = 0.1 + 0.9 * 0.5 * (1.0 - np.tanh(2.0 * (r - R) / 2.0))
+        half = (x - xa) * side >= 0
+        dens = np.where(half, np.maximum(dens, cap), dens)
+    for shift in (0, 320):
+        d = A.dynamic_angles(np.roll(dens, shift, axis=1), phi, 1.0, 0.1)
+        assert abs(d.theta_adv_deg - 70.0) < 1.0 and abs(d.theta_rec_deg - 50.0) < 1.0, d
