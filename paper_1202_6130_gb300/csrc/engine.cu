@@ -183,15 +183,16 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
 
 // Rows per CTA segment.  Measured on GB300 (8192x4096 D2Q9 sweep): short
 // segments run fastest -- many waves of short CTAs keep the concurrently
-// active tiles in a compact band of rows and balance the SMs dynamically, and
-// the 2R halo rows a segment shares with the one below are then still in L2.
-// FP32 is fastest near 12-24 rows, 16-bit storage near 24, FP64 near 64.  Small
+// active tiles in a compact band of rows and balance the SMs dynamically; with
+// adjacent segments marching in opposite directions the 2R halo rows they
+// share are pulled at about the same time and the second pull hits in L2.
+// FP32 is fastest at 12 rows, 16-bit storage near 24, FP64 near 64.  Small
 // lattices get shorter segments so that the grid still covers at least two
 // waves of resident CTAs.
 int choose_tile_rows(int nx, int ny, int W, int esize, int R, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  int L = esize == 2 ? 24 : (esize == 4 ? 16 : 64);
+  int L = esize == 2 ? 24 : (esize == 4 ? 12 : 64);
   if (R > 1) L = std::max(L, 16 * R);
   while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
   return std::max(1, std::min(L, ny));
@@ -881,7 +882,7 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
     for (int y0 = 0; y0 < c->p.ny; y0 += L)
       for (int x0 = 0; x0 < c->p.nx; x0 += W)
-        tiles.push_back({i, x0, y0, std::min(L, c->p.ny - y0)});
+        tiles.push_back({i, x0, y0, std::min(L, c->p.ny - y0), (y0 / L) & 1});
   }
   std::vector<int32_t> first;
   std::vector<BatchTile> order;

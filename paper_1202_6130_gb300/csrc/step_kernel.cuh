@@ -155,11 +155,13 @@ __device__ __forceinline__ uint64_t step_smem_init(const StepSmem<Q, S, W, NS>& 
 // Advances one strip segment of one lattice by a time step: node rows
 // [y0, y0 + Lr) of the W columns starting at x0.  `g` counts the rows this CTA
 // has pulled so far (stage g % NS, mbarrier phase (g / NS) & 1) and is
-// advanced by Lr + 2R, so a CTA may march several segments in turn.  Returns
-// false if a stage never arrived (the status word then has kStatusTimeout).
+// advanced by Lr + 2R, so a CTA may march several segments in turn.  With
+// `rev` the segment is marched upwards (row y0 + Lr + R - 1 first); the node
+// arithmetic is the same in either direction.  Returns false if a stage never
+// arrived (the status word then has kStatusTimeout).
 template <int Q, typename S, int W, int NS, int MODE, typename Args>
 __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUtensorMap* flg,
-                                              const Args& a, int x0, int y0, int Lr,
+                                              const Args& a, int x0, int y0, int Lr, bool rev,
                                               const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                               uint64_t policy) {
   using Sh = StepShape<Q, S, W, NS>;
@@ -177,6 +179,10 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int K = Lr + 2 * R;  // node rows y0 - R .. y0 + Lr + R - 1
+  // Node row of march position k, and the march position offset of the row
+  // one above (c_y = +1): +1 marching down, -1 marching up.
+  const int ybase = rev ? y0 + Lr + R - 1 : y0 - R;
+  const int ds = rev ? -1 : 1;
   const int x = x0 + tid;
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
@@ -192,7 +198,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   auto issue = [&](int k) {
     const uint32_t gk = g0 + (uint32_t)k;
     const int s = (int)(gk % NS);
-    const int ynode = y0 - R + k;
+    const int ynode = ybase + ds * k;
     mbar_arrive_expect_tx(&bars[s], tx_bytes);
     unsigned char* st = stages + s * Sh::STAGE;
     static_for<0, Sh::NBOX>([&](auto jc) {
@@ -290,7 +296,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
 
     if (k >= 2 * R) {
       const int ko = k - R;
-      const int yo = y0 - R + ko;
+      const int yo = ybase + ds * ko;
       if constexpr (!Sh::kRegs) {
         const int so = s >= R ? s - R : s - R + NS;  // stage of row k - R
         const unsigned char* sto = stages + so * Sh::STAGE;
@@ -306,12 +312,19 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       const T uy = div_rho<T>(jy, rho, inv_rho);
 
       // sum_i w_i psi(x + c_i) c_i from the ring (rest state contributes 0).
-      const T psi_c = ring[(ko % Sh::RING_H) * Sh::RING_W + tid + Sh::RO];
+      // prow[R + c_y]: the ring row of node row yo + c_y, at this thread's column.
+      static_assert((Sh::RING_H & (Sh::RING_H - 1)) == 0, "ring height is a power of two");
+      const T* prow[2 * R + 1];
+      static_for<0, 2 * R + 1>([&](auto rc) {
+        constexpr int cy = decltype(rc)::value - R;
+        prow[R + cy] = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + tid + Sh::RO;
+      });
+      const T psi_c = prow[R][0];
       T sfx = 0, sfy = 0;
       static_for<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         if constexpr (L::cx(i) != 0 || L::cy(i) != 0) {
-          const T nb = ring[((ko + L::cy(i)) % Sh::RING_H) * Sh::RING_W + tid + Sh::RO + L::cx(i)];
+          const T nb = prow[R + L::cy(i)][L::cx(i)];
           const T wn = T(L::w(i)) * nb;
           if constexpr (L::cx(i) != 0) sfx += cmul<L::cx(i)>(wn);
           if constexpr (L::cy(i) != 0) sfy += cmul<L::cy(i)>(wn);
@@ -414,7 +427,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
 // code.
 template <typename S, int W, int NS, int MODE, typename Args>
 __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const CUtensorMap* flg,
-                                                 const Args& a, int x0, int y0, int Lr,
+                                                 const Args& a, int x0, int y0, int Lr, bool rev,
                                                  const StepSmem<9, S, W, NS>& sm, uint32_t& g) {
   constexpr int Q = 9;
   using Sh = StepShape<Q, S, W, NS>;
@@ -438,6 +451,8 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   const int xa = 2 * tid;      // first of the thread's two columns, relative to x0
   const int x = x0 + xa;
   const int K = Lr + 2 * R;
+  const int ybase = rev ? y0 + Lr + R - 1 : y0 - R;
+  const int ds = rev ? -1 : 1;
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
@@ -450,7 +465,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   auto issue = [&](int k) {
     const uint32_t gk = g0 + (uint32_t)k;
     const int s = (int)(gk % NS);
-    const int ynode = y0 - R + k;
+    const int ynode = ybase + ds * k;
     mbar_arrive_expect_tx(&bars[s], tx_bytes);
     unsigned char* st = stages + s * Sh::STAGE;
     static_for<0, Sh::NBOX>([&](auto jc) {
@@ -546,7 +561,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
 
     if (k >= 2 * R) {
       const int ko = k - R;
-      const int yo = y0 - R + ko;
+      const int yo = ybase + ds * ko;
       // rho and j of both nodes, table order.
       F2 rho = f[0], jx = f[1] - f[3], jy = f[2] - f[4];
       {
@@ -569,7 +584,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
       F2 sfx = F2::splat(0.f), sfy = F2::splat(0.f), psi_c;
       static_for<0, 3>([&](auto rc) {
         constexpr int cy = decltype(rc)::value - 1;
-        const T* row = ring + ((ko + cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa;
+        const T* row = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa;
         const float2 A = *reinterpret_cast<const float2*>(row - 2);
         const float2 B = *reinterpret_cast<const float2*>(row);
         const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
@@ -756,16 +771,20 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
 // per thread).
 template <int Q, typename S, int W, int NS, int MODE, typename Args>
 __device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensorMap* flg,
-                                          const Args& a, int x0, int y0, int Lr,
+                                          const Args& a, int x0, int y0, int Lr, bool rev,
                                           const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                           uint64_t policy) {
   if constexpr (StepShape<Q, S, W, NS>::V == 2)
-    return march_segment_v2<S, W, NS, MODE>(src, flg, a, x0, y0, Lr, sm, g);
+    return march_segment_v2<S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g);
   else
-    return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, sm, g, policy);
+    return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g, policy);
 }
 
 // One time step of one lattice: CTA (bx, by) marches strip bx, segment by.
+// Odd segments march upwards, so two vertically adjacent segments, which run
+// at about the same time, pull the rows they share (the 2R halo rows of their
+// common edge) both at their start or both at their end: the second pull of
+// such a row is an L2 hit instead of a DRAM read.
 template <int Q, typename S, int W, int NS, int MODE, int MINB>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
@@ -776,7 +795,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   const int y0 = blockIdx.y * a.tile_rows;
   uint32_t g = 0;
   march_any<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
-                               sm, g, policy);
+                               (blockIdx.y & 1u) != 0u, sm, g, policy);
 }
 
 // A lattice of a batch: TMA maps of its two population buffers and of its wall
@@ -789,9 +808,10 @@ template <typename T, typename S> struct alignas(64) BatchMember {
   int32_t cur;
 };
 
-// One segment of one member lattice.
+// One segment of one member lattice; rev != 0 marches it upwards (odd
+// segments, as in step_kernel).
 struct BatchTile {
-  int32_t member, x0, y0, rows;
+  int32_t member, x0, y0, rows, rev;
 };
 
 // One time step of every lattice of a batch.  CTA b marches tiles
@@ -818,7 +838,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     if (threadIdx.x == 0) s_args = m->args[dir];
     __syncthreads();
     if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
-                                          tile.rows, sm, g, policy))
+                                          tile.rows, tile.rev != 0, sm, g, policy))
       return;
   }
 }
