@@ -66,9 +66,17 @@ enum {
 
 enum { LBM_D2Q9 = 9, LBM_D2Q21 = 21 };
 
-/* Population storage.  FP16S / BF16S store the deviation f_i - w_i * shift_rho
- * rounded to nearest-even in 16 bits; all arithmetic is FP32. */
+/* Population storage.  FP16S / BF16S store the deviation f_i - shift_i in 16
+ * bits, shift_i = w_i * shift_rho rounded to 12 significant bits (FP16S scaled
+ * by 2^8: |f_i - shift_i| < 256, beyond which the stored value becomes inf and
+ * the non-finite check reports it); all arithmetic is FP32.  The step rounds
+ * the stored deviations stochastically by default (LBM_ROUND_STOCHASTIC: the
+ * expectation of the stored value is the FP32 value; the random bits are a
+ * counter-based hash of the node and the step, so runs are reproducible and a
+ * lattice gives the same bits alone and in a batch) or to nearest-even
+ * (LBM_ROUND_NEAREST).  Initial populations are encoded to nearest-even. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 };
+enum { LBM_ROUND_STOCHASTIC = 0, LBM_ROUND_NEAREST = 1 };
 
 /* Pseudo-potential psi(rho):
  *   LBM_PSI_EXP: rho0 * (1 - exp(-rho / rho0))          (Shan-Chen form)
@@ -97,6 +105,8 @@ typedef struct {
   double shift_rho;      /* FP16S/BF16S shift; <= 0: mean initial density */
   int32_t check_every;   /* lbm_step checks for non-finite rho every K steps; 0 = never */
   int32_t tile_rows;     /* rows per CTA strip segment; 0 = chosen by the engine */
+  int32_t rounding;      /* FP16S/BF16S: LBM_ROUND_STOCHASTIC (default) or LBM_ROUND_NEAREST */
+  int32_t reserved;      /* 0 */
 } lbm_params;
 
 /* Fills *p with defaults: D2Q9, FP32, exponential psi, tau 1, G -5.5, rho0 1,

@@ -20,6 +20,8 @@ LBM_D2Q9, LBM_D2Q21 = 9, 21
 LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
 LBM_PSI_EXP, LBM_PSI_EOS = 0, 1
 STORAGE = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+LBM_ROUND_STOCHASTIC, LBM_ROUND_NEAREST = 0, 1
+ROUNDING = {"stochastic": LBM_ROUND_STOCHASTIC, "nearest": LBM_ROUND_NEAREST}
 ERRNAMES = {LBM_EINVAL: "LBM_EINVAL", LBM_ENOMEM: "LBM_ENOMEM", LBM_ECUDA: "LBM_ECUDA",
             LBM_ESTATE: "LBM_ESTATE", LBM_ENONFINITE: "LBM_ENONFINITE",
             LBM_ETIMEOUT: "LBM_ETIMEOUT"}
@@ -34,6 +36,7 @@ class lbm_params(Structure):
         ("eos_rho1", c_double), ("eos_rho2", c_double),
         ("body_force", c_double * 2), ("shift_rho", c_double),
         ("check_every", c_int32), ("tile_rows", c_int32),
+        ("rounding", c_int32), ("reserved", c_int32),
     ]
 
 

@@ -37,7 +37,7 @@ struct lbm_ctx {
   int nchunk_pad = 0;
   CUtensorMap flag_map;
   bool has_wall = false;
-  uint32_t* d_status = nullptr;
+  uint32_t* d_status = nullptr;  // 256 bytes: word 0 status bits, words kRngWord.. step counter
   double* d_partials = nullptr;
   int nparts = 0;
   double* d_out3 = nullptr;
@@ -57,6 +57,11 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// The two step-counter words of the stochastic rounding live in the status
+// allocation (its own 64-byte line).
+constexpr int kRngWord = 16;
+
 
 thread_local std::string g_err;  // errors of calls without a context
 
@@ -253,14 +258,19 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   P.bfx = (T)p.body_force[0];
   P.bfy = (T)p.body_force[1];
   P.rho_s = (T)c->rho_s;
+  for (int i = 0; i < kMaxQ; ++i) P.shift[i] = 0.0f;
+  for (int i = 0; i < c->Q; ++i)
+    P.shift[i] = storage_shift(c->Q == 9 ? Lattice<9>::w(i) : Lattice<21>::w(i), c->rho_s);
   P.psi_kind = p.psi_kind;
   P.project = p.project;
   return P;
 }
 
 // Step arguments for a pass that reads the current buffer of c.
+// Step arguments for a pass that reads buffer `src` of c (the current one for
+// run_pass; either for the batch descriptors).
 template <int Q, typename S>
-StepArgs<typename Codec<S>::T, S> make_args(const lbm_ctx* c, S* fout, double* o_rho,
+StepArgs<typename Codec<S>::T, S> make_args(const lbm_ctx* c, int src, S* fout, double* o_rho,
                                             double* o_ux, double* o_uy, int momentum) {
   using T = typename Codec<S>::T;
   StepArgs<T, S> a{};
@@ -284,13 +294,16 @@ StepArgs<typename Codec<S>::T, S> make_args(const lbm_ctx* c, S* fout, double* o
   a.status = c->d_status;
   a.wait_ns = c->stall_wait_ns ? c->stall_wait_ns : c->wait_ns;
   a.extra_tx = c->stall_wait_ns ? 16u : 0u;
+  a.rng = c->d_status + kRngWord;
+  a.rng_idx = src;
+  a.stochastic = c->p.rounding == LBM_ROUND_STOCHASTIC ? 1 : 0;
   return a;
 }
 
 template <int Q, typename S>
 int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, int momentum,
              S* fout) {
-  const auto a = make_args<Q, S>(c, fout, o_rho, o_ux, o_uy, momentum);
+  const auto a = make_args<Q, S>(c, c->cur, fout, o_rho, o_ux, o_uy, momentum);
   // Without walls the flag map is never read; the population map stands in.
   const CUtensorMap& fm = c->has_wall ? c->flag_map : c->tmap[c->cur];
   CK(c, launch_step<Q, S>(c->tmap[c->cur], fm, a, dim3(c->grid_x, c->grid_y), c->stream, mode));
@@ -315,6 +328,8 @@ int check_params(const lbm_params* p) {
   if (p->psi_kind == LBM_PSI_EOS && !(p->eos_rho1 < p->eos_rho2))
     return fail(nullptr, LBM_EINVAL, "EOS knots must satisfy rho1 < rho2");
   if (p->check_every < 0 || p->tile_rows < 0) return fail(nullptr, LBM_EINVAL, "negative count");
+  if (p->rounding != LBM_ROUND_STOCHASTIC && p->rounding != LBM_ROUND_NEAREST)
+    return fail(nullptr, LBM_EINVAL, "rounding %d", p->rounding);
   return LBM_OK;
 }
 
@@ -503,9 +518,11 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
   });
   if (rc) return rc;
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+  CK(c, cudaMemsetAsync(c->d_status + kRngWord, 0, 2 * sizeof(uint32_t), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->has_state = true;
   c->steps = 0;
+  c->version += 1;  // the shift (step arguments) may have changed
   return LBM_OK;
 }
 
@@ -534,9 +551,11 @@ int lbm_set_equilibrium(lbm_ctx* c, const double* rho, const double* ux, const d
   });
   if (rc) return rc;
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+  CK(c, cudaMemsetAsync(c->d_status + kRngWord, 0, 2 * sizeof(uint32_t), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->has_state = true;
   c->steps = 0;
+  c->version += 1;  // the shift (step arguments) may have changed
   return LBM_OK;
 }
 
@@ -871,7 +890,7 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     m.map[1] = c->tmap[1];
     m.flags = c->has_wall ? c->flag_map : c->tmap[0];
     for (int d = 0; d < 2; ++d)
-      m.args[d] = make_args<Q, S>(c, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
+      m.args[d] = make_args<Q, S>(c, d, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
     m.cur = c->cur;
     b->versions[i] = c->version;
     b->cur0[i] = c->cur;

@@ -7,6 +7,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cstring>
+
+#include "node.cuh"
 
 namespace lbm {
 
@@ -45,33 +48,66 @@ template <int CX, int CY> __device__ __forceinline__ F2 cdot2(F2 ux, F2 uy) {
 
 // Two adjacent stored values as an F2.
 template <typename S> struct Pair;
-template <> struct Pair<float> {
-  using Raw = float2;
-  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(r); }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) { return f.v; }
-  __device__ __forceinline__ static F2 dec1(float a, float b, F2 wrs) { return F2(a, b); }
-};
 template <> struct Pair<__half> {
   using Raw = __half2;
-  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(__half22float2(r)) + wrs; }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
-    const F2 d = f - wrs;
-    return __floats2half2_rn(d.x(), d.y());
+  __device__ __forceinline__ static __half lane(Raw r, int e) { return e ? __high2half(r) : __low2half(r); }
+  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) {
+    return fma2(F2(__half22float2(r)), F2::splat(kHalfInvScale), wrs);
   }
   __device__ __forceinline__ static F2 dec1(__half a, __half b, F2 wrs) {
-    return F2(__half2float(a), __half2float(b)) + wrs;
+    return fma2(F2(__half2float(a), __half2float(b)), F2::splat(kHalfInvScale), wrs);
+  }
+  // (f - wrs) * 2^8, computed as one fused operation: exact scaling by a power
+  // of two commutes with the rounding, so it equals Codec<__half>'s value.
+  __device__ __forceinline__ static F2 scaled(F2 f, F2 wrs) {
+    return fma2(f, F2::splat(kHalfScale), -(wrs * F2::splat(kHalfScale)));
+  }
+  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
+    const F2 d = scaled(f, wrs);
+    return __floats2half2_rn(d.x(), d.y());
+  }
+  // Stochastic rounding of both lanes from one random word r (see
+  // Codec<__half>::enc_sr; first node in the low half).
+  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t r) {
+    const F2 d = scaled(f, wrs);
+    const uint32_t u = cvt_rs_f16x2(d.y(), d.x(), r);
+    Raw out;
+    static_assert(sizeof(out) == sizeof(u), "half2 is 32 bits");
+    memcpy(&out, &u, sizeof u);
+    return out;
   }
 };
 template <> struct Pair<__nv_bfloat16> {
   using Raw = __nv_bfloat162;
+  __device__ __forceinline__ static __nv_bfloat16 lane(Raw r, int e) {
+    return e ? __high2bfloat16(r) : __low2bfloat16(r);
+  }
   __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(__bfloat1622float2(r)) + wrs; }
+  __device__ __forceinline__ static F2 dec1(__nv_bfloat16 a, __nv_bfloat16 b, F2 wrs) {
+    return F2(__bfloat162float(a), __bfloat162float(b)) + wrs;
+  }
   __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
     const F2 d = f - wrs;
     return __floats2bfloat162_rn(d.x(), d.y());
   }
-  __device__ __forceinline__ static F2 dec1(__nv_bfloat16 a, __nv_bfloat16 b, F2 wrs) {
-    return F2(__bfloat162float(a), __bfloat162float(b)) + wrs;
+  // Stochastic rounding of both lanes from one random word r (see
+  // Codec<__nv_bfloat16>::enc_sr; first node in the low half).
+  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t r) {
+    const F2 d = f - wrs;
+    const uint32_t u = cvt_rs_bf16x2(d.y(), d.x(), r);
+    Raw out;
+    static_assert(sizeof(out) == sizeof(u), "bfloat162 is 32 bits");
+    memcpy(&out, &u, sizeof u);
+    return out;
   }
+};
+template <> struct Pair<float> {
+  using Raw = float2;
+  __device__ __forceinline__ static float lane(Raw r, int e) { return e ? r.y : r.x; }
+  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(r); }
+  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) { return f.v; }
+  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t) { return f.v; }
+  __device__ __forceinline__ static F2 dec1(float a, float b, F2 wrs) { return F2(a, b); }
 };
 
 }  // namespace lbm

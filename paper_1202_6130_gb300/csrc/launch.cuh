@@ -21,6 +21,9 @@ template <int Q, typename S> struct StepConfig {
                                      : (sizeof(S) == 8 ? 5 : 6);
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
                                        : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3));
+  // The batch kernel carries its tile loop on top of the march: 16-bit D2Q9
+  // targets 8 CTAs per SM there, so that it does not spill.
+  static constexpr int BATCH_MINB = (Q == 9 && sizeof(S) == 2) ? 8 : MINB;
 };
 
 template <int Q, typename S>

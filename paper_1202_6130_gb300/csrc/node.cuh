@@ -5,6 +5,7 @@
 // arithmetic the step uses.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <type_traits>
 #include <cuda_bf16.h>
@@ -15,9 +16,34 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------
-// Storage codecs.  FP64 / FP32 store f directly; FP16S / BF16S store the
-// deviation f_i - w_i rho_s rounded to nearest-even, and compute in FP32.
+// Storage codecs.  FP64 / FP32 store f directly.  FP16S / BF16S store the
+// deviation f_i - shift_i in 16 bits (FP16S scaled by kHalfScale = 2^8, so that
+// deviations down to 2.4e-7 stay in the normal range of binary16, and up to
+// 256 fit) and compute in FP32.  enc rounds to nearest-even; enc_sr rounds
+// stochastically: random bits are added below the kept mantissa of the FP32
+// value and the sum is truncated, so the stored value rounds up with
+// probability equal to the discarded fraction and its expectation is the
+// FP32 value (subnormal results included; overflow gives inf).  Round-to-
+// nearest loses every per-step increment smaller than half a unit in the last
+// place (a body force of 1e-6 adds about 3e-7 per population); the stochastic
+// version keeps them on average.
 // ---------------------------------------------------------------------------
+
+// Stochastic-rounding conversions of the sm_100 family: two FP32 values to a
+// 16-bit pair, `hi` into the upper half.  As measured on GB300, the lower half
+// takes its random bits from r[12:0] (binary16) or r[15:0] (bfloat16) and the
+// upper half from r[28:16] or r[31:16].
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float hi, float lo, uint32_t r) {
+  uint32_t u;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(u) : "f"(hi), "f"(lo), "r"(r));
+  return u;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r) {
+  uint32_t u;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(u) : "f"(hi), "f"(lo), "r"(r));
+  return u;
+}
+
 template <typename S> struct Codec;
 
 template <> struct Codec<double> {
@@ -25,6 +51,7 @@ template <> struct Codec<double> {
   static constexpr bool kShifted = false;
   __device__ __forceinline__ static T dec(double v, T) { return v; }
   __device__ __forceinline__ static double enc(T f, T) { return f; }
+  __device__ __forceinline__ static double enc_sr(T f, T, uint32_t) { return f; }
 };
 
 template <> struct Codec<float> {
@@ -32,25 +59,88 @@ template <> struct Codec<float> {
   static constexpr bool kShifted = false;
   __device__ __forceinline__ static T dec(float v, T) { return v; }
   __device__ __forceinline__ static float enc(T f, T) { return f; }
+  __device__ __forceinline__ static float enc_sr(T f, T, uint32_t) { return f; }
 };
+
+constexpr float kHalfScale = 256.0f;
+constexpr float kHalfInvScale = 1.0f / 256.0f;
 
 template <> struct Codec<__half> {
   using T = float;
   static constexpr bool kShifted = true;
-  __device__ __forceinline__ static T dec(__half v, T wrs) { return __half2float(v) + wrs; }
-  __device__ __forceinline__ static __half enc(T f, T wrs) { return __float2half_rn(f - wrs); }
+  __device__ __forceinline__ static T dec(__half v, T wrs) {
+    return fmaf(__half2float(v), kHalfInvScale, wrs);
+  }
+  // (f - wrs) * 2^8 with explicitly rounded operations: no kernel may contract
+  // it differently (a product w_i rho_s hoisted in one kernel and fused in
+  // another would change the last bit).
+  __device__ __forceinline__ static float scaled(T f, T wrs) {
+    return __fmul_rn(__fsub_rn(f, wrs), kHalfScale);
+  }
+  __device__ __forceinline__ static __half enc(T f, T wrs) { return __float2half_rn(scaled(f, wrs)); }
+  // r: random word (bits 12..0 are used).
+  __device__ __forceinline__ static __half enc_sr(T f, T wrs, uint32_t r) {
+    return __ushort_as_half((unsigned short)(cvt_rs_f16x2(0.0f, scaled(f, wrs), r) & 0xFFFFu));
+  }
 };
 
 template <> struct Codec<__nv_bfloat16> {
   using T = float;
   static constexpr bool kShifted = true;
+  // Explicitly rounded add / subtract, as for FP16S.
   __device__ __forceinline__ static T dec(__nv_bfloat16 v, T wrs) {
-    return __bfloat162float(v) + wrs;
+    return __fadd_rn(__bfloat162float(v), wrs);
   }
   __device__ __forceinline__ static __nv_bfloat16 enc(T f, T wrs) {
-    return __float2bfloat16_rn(f - wrs);
+    return __float2bfloat16_rn(__fsub_rn(f, wrs));
+  }
+  // r: random word (bits 15..0 are used).
+  __device__ __forceinline__ static __nv_bfloat16 enc_sr(T f, T wrs, uint32_t r) {
+    return __ushort_as_bfloat16(
+        (unsigned short)(cvt_rs_bf16x2(0.0f, __fsub_rn(f, wrs), r) & 0xFFFFu));
   }
 };
+
+// Storage shift of population i for FP16S / BF16S: w_i rho_s rounded to 12
+// significant bits.  Any constant serves as the shift, as long as encode and
+// decode use the same one; a short mantissa makes the FP32 decode dev + shift
+// and the encode f - shift exact in nearly all cases.  With the full product
+// w_i rho_s (w_i = 1/9, 1/36, ...) the decode rounded every stored value of a
+// population the same way, which drifted the mass by about 1e-8 per node and
+// step.  Computed in FP64 with exact scalings, so host and device agree.
+__host__ __device__ inline float storage_shift(double w, double rho_s) {
+  const double x = w * rho_s;
+  if (!(x > 0.0)) return 0.0f;
+  int e = 0;
+  (void)frexp(x, &e);
+  return (float)ldexp(nearbyint(ldexp(x, 12 - e)), e - 12);
+}
+
+constexpr int kMaxQ = 21;
+
+// Random bits for stochastic rounding, drawn from a counter: one 32-bit word
+// per (node pair, row, step) by the "lowbias32" integer hash (C. Wellons,
+// hash-prospector) of a linear key, then one word per population i as the
+// product with an odd multiplier (the splitmix64 output function of i + 1,
+// made odd).  A paired encode gives the word to one conversion (first node:
+// the low bits, see cvt_rs_f16x2); a one-node encode uses its low bits.
+__host__ __device__ constexpr uint32_t sr_multiplier(int i) {
+  uint64_t z = (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (uint32_t)z | 1u;
+}
+
+__device__ __forceinline__ uint32_t sr_hash(uint32_t x, uint32_t y, uint32_t step) {
+  uint32_t h = x * 0x9E3779B1u + y * 0x85EBCA77u + step * 0xC2B2AE3Du;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
+}
 
 // Ghost widths of the padded population layout.  x: at least 2R columns (the
 // halo node's own pull) rounded up to 16 bytes so that every TMA box starts
@@ -71,7 +161,8 @@ template <typename T> struct Physics {
   T inv_rho0;        // 1 / rho0
   T eos_tv, eos_tu, eos_tl, eos_r1, eos_r2, eos_p1, eos_p2;
   T bfx, bfy;        // body-force density
-  T rho_s;           // FP16S / BF16S shift
+  T rho_s;           // FP16S / BF16S shift density
+  float shift[kMaxQ];  // FP16S / BF16S: storage_shift(w_i, rho_s) per population
   int32_t psi_kind;  // 0 exp, 1 EOS
   int32_t project;   // projection step on/off
 };
@@ -90,6 +181,13 @@ template <typename T> struct WallFields {
 template <typename T> __device__ __forceinline__ T t_exp(T v);
 template <> __device__ __forceinline__ double t_exp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float t_exp<float>(float v) { return expf(v); }
+template <typename T> __device__ __forceinline__ T t_fma(T a, T b, T c);
+template <> __device__ __forceinline__ double t_fma<double>(double a, double b, double c) {
+  return fma(a, b, c);
+}
+template <> __device__ __forceinline__ float t_fma<float>(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
 template <typename T> __device__ __forceinline__ T t_sqrt(T v);
 template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
 template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
@@ -106,13 +204,14 @@ __device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
   }
   constexpr T theta = T(Lattice<Q>::THETA);
   T p;
+  // Explicit fused operations: the same rounding in every kernel.
   if (rho <= P.eos_r1)
     p = rho * P.eos_tv;
   else if (rho <= P.eos_r2)
-    p = P.eos_p1 + (rho - P.eos_r1) * P.eos_tu;
+    p = t_fma<T>(rho - P.eos_r1, P.eos_tu, P.eos_p1);
   else
-    p = P.eos_p2 + (rho - P.eos_r2) * P.eos_tl;
-  T arg = T(2) * (rho * theta - p);
+    p = t_fma<T>(rho - P.eos_r2, P.eos_tl, P.eos_p2);
+  T arg = T(2) * t_fma<T>(rho, theta, -p);
   return t_sqrt<T>(arg > T(0) ? arg : T(0));
 }
 

@@ -52,7 +52,7 @@ static cudaError_t prepare_batch_kernel() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   static cudaError_t once = cudaFuncSetAttribute(
-      batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>,
+      batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>,
       cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   return once;
 }
@@ -65,7 +65,7 @@ cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
   using Sh = ConfigShape<Q, S>;
   cudaError_t e = prepare_batch_kernel<Q, S>();
   if (e != cudaSuccess) return e;
-  batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>
+  batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>
       <<<nctas, Sh::NT, Sh::SMEM, stream>>>(members, tiles, first, parity);
   return cudaGetLastError();
 }
@@ -76,7 +76,7 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   if (prepare_batch_kernel<Q, S>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB>, Sh::NT, Sh::SMEM) !=
+          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>, Sh::NT, Sh::SMEM) !=
       cudaSuccess)
     return 0;
   return n;

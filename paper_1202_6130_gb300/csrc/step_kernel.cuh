@@ -56,7 +56,27 @@ template <typename T, typename S> struct StepArgs {
   uint32_t* status;    // error bits (kStatus*)
   uint64_t wait_ns;    // bound of every stage wait
   uint32_t extra_tx;   // test hook: bytes each stage expects beyond its copies (0 normally)
+  // Step counter of the stochastic rounding: two words indexed by the source
+  // buffer; a step reads rng[rng_idx] and one CTA writes rng[rng_idx ^ 1] =
+  // rng[rng_idx] + 1 for the next step (kModeStep only).
+  uint32_t* rng;
+  int32_t rng_idx;
+  int32_t stochastic;  // 16-bit storage: 1 = stochastic rounding, 0 = nearest-even
 };
+
+// Counter of the step about to run (0 unless it is needed).
+template <typename S, int MODE, typename Args>
+__device__ __forceinline__ uint32_t step_key(const Args& a) {
+  if constexpr (MODE == kModeStep && Codec<S>::kShifted) {
+    if (a.stochastic) return a.rng[a.rng_idx];
+  }
+  return 0u;
+}
+
+// Advances the counter for the next step; called by one thread of one CTA.
+template <int MODE, typename Args> __device__ __forceinline__ void advance_key(const Args& a) {
+  if constexpr (MODE == kModeStep) a.rng[a.rng_idx ^ 1] = a.rng[a.rng_idx] + 1u;
+}
 
 template <int Q, typename S, int W, int NS> struct StepShape {
   using L = Lattice<Q>;
@@ -189,6 +209,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
+  const uint32_t key = step_key<S, MODE>(a);
 
   // Every thread is done with the stages and ring of the previous segment.
   __syncthreads();
@@ -220,13 +241,12 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
     issued = n0;
   }
 
-  const T rho_s = a.phys.rho_s;
   // Population I of node column xl (relative to x0) from a stage: pulled from
   // column xl - c_x of its box row, whose first element is node column -GX.
   auto load_pop = [&](const S* st, auto ic, int xl) -> T {
     constexpr int i = decltype(ic)::value;
     constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-    return C::dec(st[off + xl], T(L::w(i)) * rho_s);
+    return C::dec(st[off + xl], T(a.phys.shift[i]));
   };
   auto psi_at = [&](const S* st, int xl) -> T {
     T rho = 0;
@@ -355,11 +375,31 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
           const T usy = uy + div_rho<T>(Fy, rho, inv_rho);
           if (a.phys.project) project<Q, T>(f, rho, jx, jy);
           node_collide<Q, T>(a.phys, f, rho, ux, uy, usx, usy);
-          // Primary store plus periodic images inside the ghost frame.
+          // Encode once (stochastic rounding draws its bits from the node and
+          // the step), then the primary store plus periodic images inside the
+          // ghost frame.
+          S e[Q];
+          if constexpr (C::kShifted) {
+            if (a.stochastic) {
+              const uint32_t h = sr_hash((uint32_t)x, (uint32_t)yo, key);
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                e[i] = C::enc_sr(f[i], T(a.phys.shift[i]), h * sr_multiplier(i));
+              });
+            } else {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                e[i] = C::enc(f[i], T(a.phys.shift[i]));
+              });
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) e[i] = C::enc(f[i], T(0));
+          }
           S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
           static_for<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            out[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i], T(L::w(i)) * rho_s);
+            out[Planes<Q>::template plane<i> * a.plane] = e[i];
           });
           // Periodic images exist only for nodes within GX of a side or GY of
           // the top or bottom; the strip test is per CTA, the row test per row.
@@ -376,7 +416,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
                 S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
                 static_for<0, Q>([&](auto ic) {
                   constexpr int i = decltype(ic)::value;
-                  o2[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i], T(L::w(i)) * rho_s);
+                  o2[Planes<Q>::template plane<i> * a.plane] = e[i];
                 });
               }
             }
@@ -459,6 +499,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   const bool pair_ok = x + 1 < a.nx;  // both nodes exist
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
+  const uint32_t key = step_key<S, MODE>(a);
 
   __syncthreads();
 
@@ -485,13 +526,12 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     issued = n0;
   }
 
-  const T rho_s = a.phys.rho_s;
   // Population I of the thread's two columns: an aligned pair when c_x is even
   // (one access), else two single loads.
   auto load_pair = [&](const S* st, auto ic) -> F2 {
     constexpr int i = decltype(ic)::value;
     constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-    const F2 wrs = F2::splat(T(L::w(i)) * rho_s);
+    const F2 wrs = F2::splat(a.phys.shift[i]);
     if constexpr ((off & 1) == 0) {
       return PR::dec(*reinterpret_cast<const typename PR::Raw*>(st + off + xa), wrs);
     } else {
@@ -503,7 +543,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     static_for<0, Q>([&](auto ic) {
       constexpr int i = decltype(ic)::value;
       constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-      const T v = C::dec(st[off + xl], T(L::w(i)) * rho_s);
+      const T v = C::dec(st[off + xl], a.phys.shift[i]);
       rho = (i == 0) ? v : rho + v;
     });
     return pseudo_potential<Q, T>(a.phys, rho);
@@ -690,17 +730,37 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
             moving += f[8];
             f[0] = rho - moving;
           }
+          // Encode both nodes once (stochastic rounding: bits from the node pair
+          // and the step), then the primary store plus periodic images.
+          typename PR::Raw raw[Q];
+          if constexpr (C::kShifted) {
+            if (a.stochastic) {
+              const uint32_t h = sr_hash((uint32_t)x, (uint32_t)yo, key);
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                raw[i] = PR::enc_sr(f[i], F2::splat(a.phys.shift[i]), h * sr_multiplier(i));
+              });
+            } else {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                raw[i] = PR::enc(f[i], F2::splat(a.phys.shift[i]));
+              });
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) raw[i] = PR::enc(f[i], F2::splat(0.f));
+          }
           S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
           if (pair_ok) {
             static_for<0, Q>([&](auto ic) {
               constexpr int i = decltype(ic)::value;
               *reinterpret_cast<typename PR::Raw*>(out + Planes<Q>::template plane<i> * a.plane) =
-                  PR::enc(f[i], F2::splat(T(L::w(i)) * rho_s));
+                  raw[i];
             });
           } else {
             static_for<0, Q>([&](auto ic) {
               constexpr int i = decltype(ic)::value;
-              out[Planes<Q>::template plane<i> * a.plane] = C::enc(f[i].x(), T(L::w(i)) * rho_s);
+              out[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], 0);
             });
           }
           const bool edge = (strip_edge && (x < GX || x + 1 >= a.nx - GX)) || yo < GY ||
@@ -720,8 +780,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
                   S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
                   static_for<0, Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    const T v = e == 0 ? f[i].x() : f[i].y();
-                    o2[Planes<Q>::template plane<i> * a.plane] = C::enc(v, T(L::w(i)) * rho_s);
+                    o2[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], e);
                   });
                 }
               }
@@ -794,6 +853,9 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   const uint64_t policy = step_smem_init(sm);
   const int y0 = blockIdx.y * a.tile_rows;
   uint32_t g = 0;
+  // Every CTA reads the counter in march_any before this launch ends; the
+  // word written here is read only by the next step.
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) advance_key<MODE>(a);
   march_any<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
                                (blockIdx.y & 1u) != 0u, sm, g, policy);
 }
@@ -835,7 +897,10 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     const auto* m = &members[tile.member];
     const int dir = (m->cur ^ parity) & 1;
     __syncthreads();  // the previous tile no longer reads s_args
-    if (threadIdx.x == 0) s_args = m->args[dir];
+    if (threadIdx.x == 0) {
+      s_args = m->args[dir];
+      if (tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(m->args[dir]);
+    }
     __syncthreads();
     if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
                                           tile.rows, tile.rev != 0, sm, g, policy))

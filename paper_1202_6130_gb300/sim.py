@@ -58,7 +58,7 @@ class Simulation:
                  tau: float = 1.0, G: float = -5.5, rho0: float = 1.0, psi_kind: int = 0,
                  project: bool = False, body_force=(0.0, 0.0), shift_rho: float = 0.0,
                  eos=None, check_every: int = 0, tile_rows: int = 0, stream=None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, rounding: str = "stochastic"):
         import torch
         self.lib = L.load()
         p = L.lbm_params()
@@ -72,6 +72,7 @@ class Simulation:
         p.body_force[0], p.body_force[1] = float(body_force[0]), float(body_force[1])
         p.shift_rho = float(shift_rho)
         p.check_every, p.tile_rows = int(check_every), int(tile_rows)
+        p.rounding = L.ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
         self.params = p
         self.nx, self.ny, self.Q = int(nx), int(ny), int(lattice)
         self.device = torch.device("cuda", torch.cuda.current_device())

@@ -30,7 +30,16 @@ import numpy as np
 from . import analysis
 from .sim import Batch, Simulation, wall_gaussian_filter
 
-STORAGES = ("fp64", "fp32", "fp16s", "bf16s")
+STORAGES = ("fp64", "fp32", "fp16s", "bf16s", "fp16s-rn", "bf16s-rn")
+
+
+def storage_kw(label: str) -> dict:
+    """Simulation keywords of a storage label: "fp16s" / "bf16s" round the
+    stored deviations stochastically (the default), "fp16s-rn" / "bf16s-rn"
+    to nearest-even."""
+    if label.endswith("-rn"):
+        return {"storage": label[:-3], "rounding": "nearest"}
+    return {"storage": label}
 
 
 def _run_batch(sims, steps: int, chunk: int, on_chunk=None):
@@ -58,7 +67,7 @@ def contact_angle_sweep(storages=STORAGES, steps: int = 50000, chunk: int = 1000
     for st in storages:
         ws = [W.droplet_on_wall(nx=nx, ny=ny, R=R, G_A=ga, G_R=G_R, noise_amp=1e-6, seed=0)
               for ga in gas]
-        sims = [Simulation.from_workload(w, storage=st) for w in ws]
+        sims = [Simulation.from_workload(w, **storage_kw(st)) for w in ws]
         m0 = [s.totals()[0] for s in sims]
         hist = {i: [] for i in range(len(sims))}
 
@@ -100,7 +109,7 @@ def slip_study(storages=STORAGES, nx: int = 8, ny: int = 256, steps: int = 30000
         res = {}
         for eps in epsilons:
             w = W.poiseuille_channel(nx=nx, ny=ny, force=force, epsilon=eps)
-            sim = Simulation.from_workload(w, storage=st)
+            sim = Simulation.from_workload(w, **storage_kw(st))
             hist = []
 
             def record(done):
@@ -125,7 +134,7 @@ def slip_study(storages=STORAGES, nx: int = 8, ny: int = 256, steps: int = 30000
     return out
 
 
-def large_precision(storages=("fp32", "fp16s", "bf16s"), steps: int = 20000):
+def large_precision(storages=("fp32", "fp16s", "bf16s", "fp16s-rn", "bf16s-rn"), steps: int = 20000):
     """8192x4096 multi-drop lattice: each storage precision against FP64 storage
     after `steps` steps (mass drift, density differences)."""
     import workloads as W
@@ -139,7 +148,7 @@ def large_precision(storages=("fp32", "fp16s", "bf16s"), steps: int = 20000):
     out = {"steps": steps, "fp64": {"mass_drift_rel": (ref.totals()[0] - m0) / m0, "wall_s": t64}}
     ref.close()
     for st in storages:
-        sim = Simulation.from_workload(w, storage=st)
+        sim = Simulation.from_workload(w, **storage_kw(st))
         a = sim.totals()[0]
         sim.step(steps)
         rho = sim.moments()[0]

@@ -43,16 +43,18 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
 
 def test_struct_sizes_match_header(lib):
     from paper_1202_6130_gb300 import _lib
-    # 6 int32 + 8 doubles + 2 doubles + 1 double + 2 int32 -> 6*4 + 11*8 + 8 = 120 (aligned)
-    assert ctypes.sizeof(_lib.lbm_params) == 120
+    # 6 int32 + 8 doubles + 2 doubles + 1 double + 4 int32 -> 6*4 + 11*8 + 16 = 128 (aligned)
+    assert ctypes.sizeof(_lib.lbm_params) == 128
     p = _lib.lbm_params()
     assert lib.lbm_params_default(ctypes.byref(p)) == 0
     assert p.nx == 128 and p.ny == 64 and p.lattice == 9 and p.storage == _lib.LBM_FP32
+    assert p.rounding == _lib.LBM_ROUND_STOCHASTIC
     assert p.tau == 1.0 and p.G == -5.5 and p.eos_rho1 == 0.222 and p.eos_rho2 == 0.869
 
 
 @pytest.mark.parametrize("field,value", [("tau", 0.5), ("nx", 0), ("lattice", 7), ("storage", 9),
-                                         ("psi_kind", 3), ("rho0", 0.0), ("check_every", -1)])
+                                         ("psi_kind", 3), ("rho0", 0.0), ("check_every", -1),
+                                         ("rounding", 2)])
 def test_create_rejects_invalid_parameters_without_touching_the_gpu(lib, field, value):
     from paper_1202_6130_gb300 import _lib
     p = _lib.lbm_params()

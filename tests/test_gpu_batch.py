@@ -37,15 +37,15 @@ def _cases():
     return out
 
 
-def _alone(pkg, w, storage, n):
-    sim = pkg.Simulation.from_workload(w, storage=storage)
+def _alone(pkg, w, storage, n, **kw):
+    sim = pkg.Simulation.from_workload(w, storage=storage, **kw)
     sim.step(n)
     f = sim.populations()
     sim.close()
     return f
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s", "bf16s"])
 @pytest.mark.parametrize("tiling", [(0, 0), (8, 0), (16, 300), (5, 7)])
 def test_batch_equals_members_alone_bitwise(pkg, storage, tiling):
     ws = _cases()
@@ -95,4 +95,51 @@ def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
     assert best["tile_rows"] in (4, 8, 16, 32, 64) and best["ms_per_step"] > 0
     b.step(3)
     assert np.isfinite(a.moments()[0]).all()
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s", "bf16s"])
+def test_d2q21_paper_fluid_batch_equals_members_alone_bitwise(pkg, storage):
+    """D2Q21 (one node per thread) with the Eq. EOS pseudo-potential and the
+    projection step; one member also has a body force."""
+    th = 2.0 / 3.0
+    kw = dict(eos=(0.25 * th, -0.25 * th, th, 0.222, 0.869), project=True)
+    ws = []
+    for k, (nx, ny) in enumerate([(96, 48), (131, 40)]):
+        w = W.droplet_on_wall(nx=nx, ny=ny, R=14.0, lattice=21, seed=40 + k, noise_amp=1e-5,
+                              tau=0.8 + 0.3 * k, G=-1.0 / th, G_A=0.3, G_R=1.33, rho_l=1.0,
+                              rho_v=0.1)
+        w.psi_kind = 1
+        if k == 1:
+            w.body_force = (2e-6, 0.0)
+        ws.append(w)
+    want = [_alone(pkg, w, storage, 9, **kw) for w in ws]
+    sims = [pkg.Simulation.from_workload(w, storage=storage, **kw) for w in ws]
+    b = pkg.Batch()
+    for sm in sims:
+        b.add(sm)
+    b.step(4)
+    b.step(5)
+    for sm, f in zip(sims, want):
+        np.testing.assert_array_equal(sm.populations(), f)
+    b.close()
+
+
+def test_member_reinitialised_between_batch_steps(pkg):
+    """Setting a member's populations again (new 16-bit storage shift, step
+    counter back to 0) makes the batch rebuild that member's step arguments."""
+    ws = _cases()[:2]
+    sims = [pkg.Simulation.from_workload(w, storage="fp16s") for w in ws]
+    b = pkg.Batch()
+    for s in sims:
+        b.add(s)
+    b.step(3)
+    w2 = W.droplet_on_wall(nx=ws[1].nx, ny=ws[1].ny, R=10.0, seed=77, rho_l=1.2, rho_v=0.3)
+    sims[1].set_equilibrium(w2.rho, w2.ux, w2.uy)
+    b.step(4)
+    ref = pkg.Simulation.from_workload(ws[1], storage="fp16s")
+    ref.set_equilibrium(w2.rho, w2.ux, w2.uy)
+    ref.step(4)
+    np.testing.assert_array_equal(sims[1].populations(), ref.populations())
+    np.testing.assert_array_equal(sims[0].populations(), _alone(pkg, ws[0], "fp16s", 7))
     b.close()
