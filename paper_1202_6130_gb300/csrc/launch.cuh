@@ -13,14 +13,15 @@ namespace lbm {
 // CTA width, TMA pipeline depth and the CTAs per SM the register budget is
 // sized for, per (lattice, storage).  Shared memory per CTA is
 // NS * (Q box slots + flag slot) + the psi ring.
-// (D2Q9 FP32 and 16-bit values measured on GB300: NS 4 / MINB 8 for FP32 and
-// MINB 10 for 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12.)
+// (Measured on GB300, 8192x4096: D2Q9 NS 4 / MINB 8 for FP32 and MINB 10 for
+// 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12; D2Q21 needs NS >= R + 2
+// = 5, and NS 5 with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3
+// by 21% and 5%.)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
-  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6))
-                                     : (sizeof(S) == 8 ? 5 : 6);
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6)) : 5;
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
-                                       : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3));
+                                       : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 5));
   // The batch kernel carries its tile loop on top of the march: 16-bit D2Q9
   // targets 8 CTAs per SM there, so that it does not spill.
   static constexpr int BATCH_MINB = (Q == 9 && sizeof(S) == 2) ? 8 : MINB;

@@ -367,3 +367,23 @@ def test_stage_wait_runs_out_and_reports_timeout(pkg):
     ref = make_sim(pkg, w, "fp32")
     ref.step(5)
     np.testing.assert_array_equal(sim.populations(), ref.populations())
+
+
+def test_fp64_channel_slip_length_matches_oracle(pkg):
+    """Body-force-driven liquid channel (x-invariant, so an 8-wide slice):
+    the slip length b = u(y_w)/|u'(y_w)| from the bulk parabola of the FP64
+    GPU run equals the oracle's to 1e-10, for both wall roughness exponents;
+    the velocity field agrees to 1e-11 of its maximum after 3000 steps."""
+    from paper_1202_6130_gb300 import analysis as A
+    for eps in (1.0, 1.3):
+        w = W.poiseuille_channel(nx=8, ny=96, force=1e-6, epsilon=eps)
+        _, rho_o, ux_o, _ = run_oracle(w, 3000)
+        sim = make_sim(pkg, w, "fp64")
+        sim.step(3000)
+        rho_g, ux_g, _ = sim.moments()
+        sim.close()
+        b_o = A.slip_length(ux_o, w.phi_s).slip_length
+        b_g = A.slip_length(ux_g, w.phi_s).slip_length
+        du = np.max(np.abs(ux_g - ux_o)) / np.max(np.abs(ux_o))
+        assert abs(b_g - b_o) <= 1e-10 * abs(b_o), (eps, b_g, b_o, du)
+        assert du <= 1e-11, (eps, du)
