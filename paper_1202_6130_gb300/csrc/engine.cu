@@ -258,9 +258,12 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   P.bfx = (T)p.body_force[0];
   P.bfy = (T)p.body_force[1];
   P.rho_s = (T)c->rho_s;
-  for (int i = 0; i < kMaxQ; ++i) P.shift[i] = 0.0f;
-  for (int i = 0; i < c->Q; ++i)
+  for (int i = 0; i < kMaxQ; ++i) P.shift[i] = P.enc_add[i] = 0.0f;
+  for (int i = 0; i < c->Q; ++i) {
     P.shift[i] = storage_shift(c->Q == 9 ? Lattice<9>::w(i) : Lattice<21>::w(i), c->rho_s);
+    // exact: a 12-bit shift times a power of two
+    P.enc_add[i] = c->p.storage == LBM_FP16S ? -kHalfScale * P.shift[i] : -P.shift[i];
+  }
   P.psi_kind = p.psi_kind;
   P.project = p.project;
   return P;

@@ -57,19 +57,20 @@ template <> struct Pair<__half> {
   __device__ __forceinline__ static F2 dec1(__half a, __half b, F2 wrs) {
     return fma2(F2(__half2float(a), __half2float(b)), F2::splat(kHalfInvScale), wrs);
   }
-  // (f - wrs) * 2^8, computed as one fused operation: exact scaling by a power
-  // of two commutes with the rounding, so it equals Codec<__half>'s value.
-  __device__ __forceinline__ static F2 scaled(F2 f, F2 wrs) {
-    return fma2(f, F2::splat(kHalfScale), -(wrs * F2::splat(kHalfScale)));
+  // add = -2^8 shift: (f - shift) * 2^8 as one fused operation.  Exact
+  // scaling by a power of two commutes with the rounding, so it equals
+  // Codec<__half>'s value.
+  __device__ __forceinline__ static F2 scaled(F2 f, F2 add) {
+    return fma2(f, F2::splat(kHalfScale), add);
   }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
-    const F2 d = scaled(f, wrs);
+  __device__ __forceinline__ static Raw enc(F2 f, F2 add) {
+    const F2 d = scaled(f, add);
     return __floats2half2_rn(d.x(), d.y());
   }
   // Stochastic rounding of both lanes from one random word r (see
   // Codec<__half>::enc_sr; first node in the low half).
-  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t r) {
-    const F2 d = scaled(f, wrs);
+  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 add, uint32_t r) {
+    const F2 d = scaled(f, add);
     const uint32_t u = cvt_rs_f16x2(d.y(), d.x(), r);
     Raw out;
     static_assert(sizeof(out) == sizeof(u), "half2 is 32 bits");
@@ -86,14 +87,15 @@ template <> struct Pair<__nv_bfloat16> {
   __device__ __forceinline__ static F2 dec1(__nv_bfloat16 a, __nv_bfloat16 b, F2 wrs) {
     return F2(__bfloat162float(a), __bfloat162float(b)) + wrs;
   }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) {
-    const F2 d = f - wrs;
+  // add = -shift.
+  __device__ __forceinline__ static Raw enc(F2 f, F2 add) {
+    const F2 d = f + add;
     return __floats2bfloat162_rn(d.x(), d.y());
   }
   // Stochastic rounding of both lanes from one random word r (see
   // Codec<__nv_bfloat16>::enc_sr; first node in the low half).
-  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t r) {
-    const F2 d = f - wrs;
+  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 add, uint32_t r) {
+    const F2 d = f + add;
     const uint32_t u = cvt_rs_bf16x2(d.y(), d.x(), r);
     Raw out;
     static_assert(sizeof(out) == sizeof(u), "bfloat162 is 32 bits");

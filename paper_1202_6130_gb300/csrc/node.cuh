@@ -163,6 +163,9 @@ template <typename T> struct Physics {
   T bfx, bfy;        // body-force density
   T rho_s;           // FP16S / BF16S shift density
   float shift[kMaxQ];  // FP16S / BF16S: storage_shift(w_i, rho_s) per population
+  // What the paired encoder adds after its scaling: -2^8 shift_i (FP16S) or
+  // -shift_i (BF16S), so that the encode is one fused operation.
+  float enc_add[kMaxQ];
   int32_t psi_kind;  // 0 exp, 1 EOS
   int32_t project;   // projection step on/off
 };

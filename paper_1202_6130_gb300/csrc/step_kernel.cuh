@@ -738,12 +738,12 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
               const uint32_t h = sr_hash((uint32_t)x, (uint32_t)yo, key);
               static_for<0, Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                raw[i] = PR::enc_sr(f[i], F2::splat(a.phys.shift[i]), h * sr_multiplier(i));
+                raw[i] = PR::enc_sr(f[i], F2::splat(a.phys.enc_add[i]), h * sr_multiplier(i));
               });
             } else {
               static_for<0, Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                raw[i] = PR::enc(f[i], F2::splat(a.phys.shift[i]));
+                raw[i] = PR::enc(f[i], F2::splat(a.phys.enc_add[i]));
               });
             }
           } else {
@@ -897,10 +897,14 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     const auto* m = &members[tile.member];
     const int dir = (m->cur ^ parity) & 1;
     __syncthreads();  // the previous tile no longer reads s_args
-    if (threadIdx.x == 0) {
-      s_args = m->args[dir];
-      if (tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(m->args[dir]);
+    {  // all threads copy the member's step arguments, one word each
+      static_assert(sizeof(Args) % 4 == 0 && alignof(Args) >= 4, "word copy");
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&m->args[dir]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
+#pragma unroll 1
+      for (int k = threadIdx.x; k < (int)(sizeof(Args) / 4); k += blockDim.x) dst[k] = src[k];
     }
+    if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(m->args[dir]);
     __syncthreads();
     if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
                                           tile.rows, tile.rev != 0, sm, g, policy))
