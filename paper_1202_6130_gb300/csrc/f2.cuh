@@ -15,7 +15,7 @@ namespace lbm {
 
 struct F2 {
   float2 v;
-  __device__ __forceinline__ F2() = default;
+  F2() = default;
   __device__ __forceinline__ F2(float2 a) : v(a) {}
   __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
   __device__ __forceinline__ static F2 splat(float a) { return F2(a, a); }

@@ -266,9 +266,12 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
   int k = 0;
-  // Unrolled by two so that the populations carried from one row to the next
-  // (kRegs) alternate between register sets instead of being copied.
-#pragma unroll 2
+  // With kRegs, unrolled by two so that the populations carried from one row
+  // to the next alternate between register sets instead of being copied;
+  // otherwise not unrolled (the D2Q21 body is large enough to miss in the
+  // instruction cache when duplicated).
+  constexpr int kUnroll = Sh::kRegs ? 2 : 1;
+#pragma unroll kUnroll
   for (; k < K; ++k) {
     if (!mbar_wait_bounded(&bars[s], phase, a.wait_ns)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
 // A lattice of a batch: TMA maps of its two population buffers and of its wall
 // flags, and the step arguments for either direction (args[d] reads buffer d
 // and writes buffer 1 - d).  cur: the buffer holding the state at parity 0.
-template <typename T, typename S> struct alignas(64) BatchMember {
+template <typename T, typename S> struct BatchMember {
   CUtensorMap map[2];
   CUtensorMap flags;
   StepArgs<T, S> args[2];
