@@ -11,13 +11,16 @@ channel) and waiting requests join it, so requests that arrive while others
 are running start as soon as memory frees up.
 
 Per-request arithmetic is the same alone and in the mix: the result of a
-request does not depend on what else is in the batch.
+request does not depend on what else is in the batch.  Host work (building a
+request's fields, measuring a result) runs in worker threads and overlaps the
+GPU steps.
 """
 from __future__ import annotations
 
 import math
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 from typing import Callable, Optional
 
@@ -106,11 +109,19 @@ def measure(req: Request, w, rho, ux, uy) -> float:
 
 
 class Server:
-    """FIFO admission by device footprint; one resident batch; step quanta."""
+    """FIFO admission by device footprint; one resident batch; step quanta.
+
+    Host work overlaps the GPU.  A request's fields are built by a worker
+    thread as soon as it is submitted.  While the batch runs a quantum, the
+    main thread creates and initialises the simulations of waiting requests
+    that fit the budget, on a side stream (they join the batch at the next
+    quantum).  Finished requests are read back after the quantum and measured
+    by worker threads; a result's t_done is when its measurement completes."""
 
     def __init__(self, storage: str = "fp32", hbm_budget: float = 64e9, quantum: int = 500,
                  keep_fields: bool = False, workload: Callable = default_workload,
-                 tiling: Optional[tuple] = None):
+                 tiling: Optional[tuple] = None, host_workers: int = 4):
+        import torch
         self.storage = storage
         self.budget = float(hbm_budget)
         self.quantum = int(quantum)
@@ -119,8 +130,13 @@ class Server:
         self.batch = Batch()
         if tiling is not None:
             self.batch.set_tiling(*tiling)
+        self.side = torch.cuda.Stream()
+        self.pool = ThreadPoolExecutor(max_workers=max(1, int(host_workers)))
         self.queue: deque = deque()
+        self.fields: dict = {}      # id -> future of the request's workload
+        self.staged: list = []      # [req, sim, workload, t_admit, bytes], not yet in the batch
         self.active: dict = {}      # id -> [req, sim, workload, steps_left, t_admit, bytes]
+        self.measuring: list = []   # futures of Results
         self.used = 0.0
         self.results: list = []
         self.t0 = time.perf_counter()
@@ -132,19 +148,37 @@ class Server:
         if footprint_bytes(req.nx, req.ny, self.storage) > self.budget:
             raise ValueError(f"request {req.id} needs more than the whole HBM budget")
         self.queue.append(req)
+        self.fields[req.id] = self.pool.submit(self.workload, req)
 
-    def _admit(self):
+    def _stage(self):
+        """Creates, on the side stream, the simulations of the waiting requests
+        that fit the budget (strict FIFO: the first that does not fit waits)."""
+        import torch
         while self.queue:
             req = self.queue[0]
             need = footprint_bytes(req.nx, req.ny, self.storage)
             if self.used + need > self.budget:
-                break                                   # strict FIFO: wait for memory
+                break
             self.queue.popleft()
-            w = self.workload(req)
-            sim = Simulation.from_workload(w, storage=self.storage)
-            self.batch.add(sim)
-            self.active[req.id] = [req, sim, w, req.steps, self.now(), need]
+            w = self.fields.pop(req.id).result()
+            with torch.cuda.stream(self.side):
+                sim = Simulation.from_workload(w, storage=self.storage, stream=self.side)
+            self.staged.append([req, sim, w, self.now(), need])
             self.used += need
+
+    def _join(self):
+        for req, sim, w, t_admit, need in self.staged:
+            self.batch.add(sim)
+            self.active[req.id] = [req, sim, w, req.steps, t_admit, need]
+        self.staged.clear()
+
+    def _finish(self, req, w, t_admit, rho, ux, uy) -> Result:
+        res = Result(req.id, req.kind, req.nx, req.ny, req.steps, req.t_arrival, t_admit, 0.0,
+                     measure(req, w, rho, ux, uy))
+        if self.keep_fields:
+            res.rho, res.ux, res.uy = rho, ux, uy
+        res.t_done = self.now()
+        return res
 
     def _retire(self):
         done = [k for k, v in self.active.items() if v[3] <= 0]
@@ -152,26 +186,38 @@ class Server:
             req, sim, w, _, t_admit, need = self.active.pop(k)
             self.batch.remove(sim)
             rho, ux, uy = sim.moments()
-            res = Result(req.id, req.kind, req.nx, req.ny, req.steps, req.t_arrival, t_admit,
-                         self.now(), measure(req, w, rho, ux, uy))
-            if self.keep_fields:
-                res.rho, res.ux, res.uy = rho, ux, uy
             sim.close()
             self.used -= need
-            self.results.append(res)
+            self.measuring.append(self.pool.submit(self._finish, req, w, t_admit, rho, ux, uy))
+
+    def _collect(self, wait: bool = False):
+        pending = []
+        for f in self.measuring:
+            if wait or f.done():
+                self.results.append(f.result())
+            else:
+                pending.append(f)
+        self.measuring = pending
 
     def tick(self) -> bool:
-        """Admit, advance one quantum (or up to the nearest finish), retire.
-        Returns False when nothing is active or waiting."""
-        self._admit()
+        """Joins the staged simulations, launches one quantum (or up to the
+        nearest finish), stages waiting requests while it runs, retires.
+        Returns False when nothing is active, staged or waiting."""
+        self._join()
         if not self.active:
-            return bool(self.queue)
+            self._stage()
+            self._join()
+            if not self.active:
+                self._collect()
+                return bool(self.queue)
         q = min(self.quantum, min(v[3] for v in self.active.values()))
         self.batch.step(q)
+        self._stage()
+        self._collect()
         for v in self.active.values():
             v[3] -= q
         self._retire()
-        return bool(self.active or self.queue)
+        return bool(self.active or self.staged or self.queue)
 
     def run(self, requests, realtime: bool = True):
         """Serves `requests` (sorted by arrival).  With realtime, a request is
@@ -179,20 +225,26 @@ class Server:
         released at once."""
         pending = deque(sorted(requests, key=lambda r: r.t_arrival))
         self.t0 = time.perf_counter()
-        while pending or self.queue or self.active:
+        while pending or self.queue or self.active or self.staged:
             t = self.now()
             while pending and (not realtime or pending[0].t_arrival <= t):
                 self.submit(pending.popleft())
-            if not self.active and not self.queue and pending:
+            if not self.active and not self.queue and not self.staged and pending:
                 time.sleep(max(0.0, min(0.01, pending[0].t_arrival - t)))
                 continue
             self.tick()
+        self._collect(wait=True)
         return self.results
 
     def close(self):
         for v in self.active.values():
             v[1].close()
+        for v in self.staged:
+            v[1].close()
         self.active.clear()
+        self.staged.clear()
+        self._collect(wait=True)
+        self.pool.shutdown(wait=True)
         self.batch.close()
 
 
