@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <initializer_list>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -810,6 +811,19 @@ struct lbm_batch {
   int64_t phase = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t order_ev = nullptr;  // orders member streams with the batch stream
+  // Members are launched in chunks of up to kBatchChunk, each with its step
+  // arguments as a kernel parameter.  With several chunks every chunk has its
+  // own stream, forked from and joined back to the batch stream around each
+  // sequence of steps (a member depends only on its own previous step).
+  struct Chunk {
+    std::vector<unsigned char> args;  // host copy of BatchArgs<T, S>
+    int base = 0, count = 0;          // members [base, base + count)
+    int tile_off = 0, first_off = 0, nctas = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Chunk> chunks;
+  cudaEvent_t fork_ev = nullptr;
   std::string err;
   bool poisoned = false;
 };
@@ -876,13 +890,24 @@ void drop_graph(lbm_batch* b) {
   }
 }
 
+void release_chunk(lbm_batch::Chunk& ch) {
+  if (ch.stream) {
+    cudaStreamSynchronize(ch.stream);
+    cudaStreamDestroy(ch.stream);
+  }
+  if (ch.done) cudaEventDestroy(ch.done);
+  ch.stream = nullptr;
+  ch.done = nullptr;
+}
+
 template <int Q, typename S> int batch_build(lbm_batch* b) {
   using T = typename Codec<S>::T;
   using M = BatchMember<T, S>;
+  using A = BatchArgs<T, S>;
   constexpr int W = StepConfig<Q, S>::W;
   const int n = (int)b->members.size();
+  const int nchunk = (n + kBatchChunk - 1) / kBatchChunk;
   std::vector<M> hm(n);
-  std::vector<BatchTile> tiles;
   b->versions.assign(n, 0);
   b->cur0.assign(n, 0);
   for (int i = 0; i < n; ++i) {
@@ -892,43 +917,73 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     m.map[0] = c->tmap[0];
     m.map[1] = c->tmap[1];
     m.flags = c->has_wall ? c->flag_map : c->tmap[0];
-    for (int d = 0; d < 2; ++d)
-      m.args[d] = make_args<Q, S>(c, d, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
-    m.cur = c->cur;
     b->versions[i] = c->version;
     b->cur0[i] = c->cur;
   }
-  // Tiles in row-band-major order: all strips of a segment before the next.
-  for (int i = 0; i < n; ++i) {
-    const lbm_ctx* c = b->members[i];
-    const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
-    for (int y0 = 0; y0 < c->p.ny; y0 += L)
-      for (int x0 = 0; x0 < c->p.nx; x0 += W)
-        tiles.push_back({i, x0, y0, std::min(L, c->p.ny - y0), (y0 / L) & 1});
-  }
-  std::vector<int32_t> first;
-  std::vector<BatchTile> order;
-  if (b->ctas <= 0) {
-    b->nctas = (int)tiles.size();
-    order = tiles;
-    first.resize(tiles.size() + 1);
-    for (size_t t = 0; t <= tiles.size(); ++t) first[t] = (int32_t)t;
-  } else {
-    // Persistent CTAs, tiles dealt round-robin: CTA k gets tiles k, k + G, ...
-    b->nctas = std::min<int>(b->ctas, (int)tiles.size());
-    const int G = b->nctas;
-    first.assign(G + 1, 0);
-    for (int k = 0; k < G; ++k) {
-      first[k] = (int32_t)order.size();
-      for (size_t t = k; t < tiles.size(); t += G) order.push_back(tiles[t]);
+  for (size_t k = nchunk; k < b->chunks.size(); ++k) release_chunk(b->chunks[k]);
+  b->chunks.resize(nchunk);
+  // Tiles per chunk in row-band-major order (all strips of a segment before
+  // the next), member indices local to the chunk.
+  std::vector<std::vector<BatchTile>> ctiles(nchunk);
+  size_t total = 0;
+  for (int k = 0; k < nchunk; ++k) {
+    lbm_batch::Chunk& ch = b->chunks[k];
+    ch.base = k * kBatchChunk;
+    ch.count = std::min(kBatchChunk, n - ch.base);
+    ch.args.assign(sizeof(A), 0);
+    A* pa = reinterpret_cast<A*>(ch.args.data());
+    for (int i = 0; i < ch.count; ++i) {
+      lbm_ctx* c = b->members[ch.base + i];
+      for (int d = 0; d < 2; ++d)
+        pa->a[i][d] = make_args<Q, S>(c, d, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
+      pa->cur[i] = c->cur;
+      const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
+      for (int y0 = 0; y0 < c->p.ny; y0 += L)
+        for (int x0 = 0; x0 < c->p.nx; x0 += W)
+          ctiles[k].push_back({i, x0, y0, std::min(L, c->p.ny - y0), (y0 / L) & 1});
     }
-    first[G] = (int32_t)order.size();
+    total += ctiles[k].size();
   }
+  std::vector<BatchTile> order;
+  std::vector<int32_t> first;
+  b->nctas = 0;
+  for (int k = 0; k < nchunk; ++k) {
+    lbm_batch::Chunk& ch = b->chunks[k];
+    const std::vector<BatchTile>& tiles = ctiles[k];
+    ch.tile_off = (int)order.size();
+    ch.first_off = (int)first.size();
+    if (b->ctas <= 0) {
+      ch.nctas = (int)tiles.size();
+      order.insert(order.end(), tiles.begin(), tiles.end());
+      for (size_t t = 0; t <= tiles.size(); ++t) first.push_back((int32_t)t);
+    } else {
+      // Persistent CTAs (the batch's count shared out by tiles), tiles dealt
+      // round-robin: CTA j gets tiles j, j + G, ...
+      const int G = (int)std::max<size_t>(
+          1, std::min(tiles.size(), (size_t)std::llround((double)b->ctas * tiles.size() / total)));
+      ch.nctas = G;
+      int32_t local = 0;
+      for (int j = 0; j < G; ++j) {
+        first.push_back(local);
+        for (size_t t = j; t < tiles.size(); t += G) {
+          order.push_back(tiles[t]);
+          ++local;
+        }
+      }
+      first.push_back(local);
+    }
+    b->nctas += ch.nctas;
+    if (nchunk > 1 && !ch.stream) {
+      BCK(b, cudaStreamCreateWithFlags(&ch.stream, cudaStreamNonBlocking));
+      BCK(b, cudaEventCreateWithFlags(&ch.done, cudaEventDisableTiming));
+    }
+  }
+  if (nchunk > 1 && !b->fork_ev) BCK(b, cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
   b->ntiles = (int)order.size();
   batch_ctas_per_sm<Q, S>();  // sets the kernel's shared-memory attribute outside any capture
   int rc = bgrow(b, &b->d_members, &b->cap_members, sizeof(M) * std::max(1, n));
   if (!rc) rc = bgrow(b, &b->d_tiles, &b->cap_tiles, sizeof(BatchTile) * std::max<size_t>(1, order.size()));
-  if (!rc) rc = bgrow(b, &b->d_first, &b->cap_first, sizeof(int32_t) * first.size());
+  if (!rc) rc = bgrow(b, &b->d_first, &b->cap_first, sizeof(int32_t) * std::max<size_t>(1, first.size()));
   if (rc) return rc;
   BCK(b, cudaMemcpyAsync(b->d_members, hm.data(), sizeof(M) * n, cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaMemcpyAsync(b->d_tiles, order.data(), sizeof(BatchTile) * order.size(),
@@ -942,11 +997,21 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
   return LBM_OK;
 }
 
+// Enqueues one step of every chunk (on its own stream when there are several;
+// the caller forks and joins them).
 template <int Q, typename S> cudaError_t batch_launch(lbm_batch* b, int parity) {
   using T = typename Codec<S>::T;
-  return launch_batch<Q, S>(static_cast<const BatchMember<T, S>*>(b->d_members),
-                            static_cast<const BatchTile*>(b->d_tiles),
-                            static_cast<const int32_t*>(b->d_first), b->nctas, parity, b->stream);
+  const bool multi = b->chunks.size() > 1;
+  for (const lbm_batch::Chunk& ch : b->chunks) {
+    cudaError_t e = launch_batch<Q, S>(
+        *reinterpret_cast<const BatchArgs<T, S>*>(ch.args.data()),
+        static_cast<const BatchMember<T, S>*>(b->d_members) + ch.base,
+        static_cast<const BatchTile*>(b->d_tiles) + ch.tile_off,
+        static_cast<const int32_t*>(b->d_first) + ch.first_off, ch.nctas, parity,
+        multi ? ch.stream : b->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int batch_guard(lbm_batch* b) {
@@ -1057,27 +1122,44 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     BCK(b, cudaEventRecord(b->order_ev, ms));
     BCK(b, cudaStreamWaitEvent(b->stream, b->order_ev, 0));
   }
-  auto launch = [&](int parity) -> int {
-    return dispatch(b->Q, b->storage, [&]<int Q, typename S>() -> int {
-      BCK(b, batch_launch<Q, S>(b, parity));
-      return LBM_OK;
-    });
+  // Steps with the given parities: fork the chunk streams from the batch
+  // stream, launch each chunk's steps on its stream, join them back.
+  auto launch = [&](std::initializer_list<int> parities) -> int {
+    const bool multi = b->chunks.size() > 1;
+    if (multi) {
+      BCK(b, cudaEventRecord(b->fork_ev, b->stream));
+      for (const lbm_batch::Chunk& ch : b->chunks) BCK(b, cudaStreamWaitEvent(ch.stream, b->fork_ev, 0));
+    }
+    for (int parity : parities) {
+      const int r = dispatch(b->Q, b->storage, [&]<int Q, typename S>() -> int {
+        BCK(b, batch_launch<Q, S>(b, parity));
+        return LBM_OK;
+      });
+      if (r) return r;
+    }
+    if (multi) {
+      for (const lbm_batch::Chunk& ch : b->chunks) {
+        BCK(b, cudaEventRecord(ch.done, ch.stream));
+        BCK(b, cudaStreamWaitEvent(b->stream, ch.done, 0));
+      }
+    }
+    return LBM_OK;
   };
   int64_t left = nsteps;
   // Bring the phase to even, then replay a captured two-step graph.
   if (b->phase & 1) {
-    if ((rc = launch(1))) return rc;
+    if ((rc = launch({1}))) return rc;
     b->phase += 1;
     left -= 1;
   }
   if (left >= 2 && b->stream != nullptr && !b->gexec) {
     cudaGraph_t graph = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int r0 = launch(0), r1 = r0 ? r0 : launch(1);
+    const int r = launch({0, 1});
     cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
-    if (r0 || r1) {
+    if (r) {
       if (graph) cudaGraphDestroy(graph);
-      return r0 ? r0 : r1;
+      return r;
     }
     BCK(b, ee);
     cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
@@ -1088,13 +1170,13 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     if (b->gexec) {
       BCK(b, cudaGraphLaunch(b->gexec, b->stream));
     } else {
-      if ((rc = launch(0)) || (rc = launch(1))) return rc;
+      if ((rc = launch({0, 1}))) return rc;
     }
     b->phase += 2;
     left -= 2;
   }
   if (left == 1) {
-    if ((rc = launch(0))) return rc;
+    if ((rc = launch({0}))) return rc;
     b->phase += 1;
   }
   // Later work on a member's stream sees the batch's steps.
@@ -1116,7 +1198,7 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile
   BCK(b, cudaGetDevice(&dev));
   BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int cps = dispatch(b->Q, b->storage, [&]<int Q, typename S>() { return batch_ctas_per_sm<Q, S>(); });
-  const int rows_c[] = {4, 8, 16, 32, 64};
+  const int rows_c[] = {4, 8, 12, 16, 24, 32, 64};
   const int ctas_c[] = {0, std::max(1, cps) * sms};
   cudaEvent_t e0, e1;
   BCK(b, cudaEventCreate(&e0));
@@ -1163,6 +1245,8 @@ int lbm_batch_destroy(lbm_batch* b) {
   cudaStreamSynchronize(b->stream);
   cudaGetLastError();
   drop_graph(b);
+  for (lbm_batch::Chunk& ch : b->chunks) release_chunk(ch);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->order_ev) cudaEventDestroy(b->order_ev);
   bfree(b, b->d_members);
   bfree(b, b->d_tiles);

@@ -39,10 +39,11 @@ cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
 // CTAs of the step kernel that fit on one SM (occupancy query).
 template <int Q, typename S> int step_ctas_per_sm();
 
-// One time step of every member of a batch (CTA b marches tiles
+// One time step of up to kBatchChunk members of a batch (CTA b marches tiles
 // [first[b], first[b + 1])), and its residency per SM.
 template <int Q, typename S>
-cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
+cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
+                         const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
                          cudaStream_t stream);
 template <int Q, typename S> int batch_ctas_per_sm();

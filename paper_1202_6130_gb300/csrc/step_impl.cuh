@@ -58,7 +58,8 @@ static cudaError_t prepare_batch_kernel() {
 }
 
 template <int Q, typename S>
-cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
+cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
+                         const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
                          cudaStream_t stream) {
   using Cfg = StepConfig<Q, S>;
@@ -66,7 +67,7 @@ cudaError_t launch_batch(const BatchMember<typename Codec<S>::T, S>* members,
   cudaError_t e = prepare_batch_kernel<Q, S>();
   if (e != cudaSuccess) return e;
   batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>
-      <<<nctas, Sh::NT, Sh::SMEM, stream>>>(members, tiles, first, parity);
+      <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
   return cudaGetLastError();
 }
 
@@ -90,6 +91,7 @@ template <int Q, typename S> int batch_ctas_per_sm() {
                                               dim3, cudaStream_t, int);                    \
   template int lbm::step_ctas_per_sm<Q, S>();                                            \
   template cudaError_t lbm::launch_batch<Q, S>(                                          \
+      const lbm::BatchArgs<lbm::Codec<S>::T, S>&,                                         \
       const lbm::BatchMember<lbm::Codec<S>::T, S>*, const lbm::BatchTile*, const int32_t*, \
       int, int, cudaStream_t);                                                           \
   template int lbm::batch_ctas_per_sm<Q, S>();

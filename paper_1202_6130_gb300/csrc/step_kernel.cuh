@@ -864,32 +864,39 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
 }
 
 // A lattice of a batch: TMA maps of its two population buffers and of its wall
-// flags, and the step arguments for either direction (args[d] reads buffer d
-// and writes buffer 1 - d).  cur: the buffer holding the state at parity 0.
+// flags (in device memory; map[d] reads buffer d).
 template <typename T, typename S> struct BatchMember {
   CUtensorMap map[2];
   CUtensorMap flags;
-  StepArgs<T, S> args[2];
-  int32_t cur;
 };
 
-// One segment of one member lattice; rev != 0 marches it upwards (odd
-// segments, as in step_kernel).
+// Step arguments of up to kBatchChunk members of a batch for either direction
+// (a[m][d] reads buffer d and writes buffer 1 - d), and the buffer holding
+// each member's state at parity 0.  Passed as a kernel parameter, so the
+// kernel reads them from constant memory: read-only, unlike a copy in shared
+// memory that every per-row barrier would force the compiler to reload.
+constexpr int kBatchChunk = 32;
+template <typename T, typename S> struct BatchArgs {
+  StepArgs<T, S> a[kBatchChunk][2];
+  int32_t cur[kBatchChunk];
+};
+
+// One segment of one member lattice (member: index within the launch's chunk);
+// rev != 0 marches it upwards (odd segments, as in step_kernel).
 struct BatchTile {
   int32_t member, x0, y0, rows, rev;
 };
 
-// One time step of every lattice of a batch.  CTA b marches tiles
+// One time step of up to kBatchChunk lattices of a batch.  CTA b marches tiles
 // [first[b], first[b + 1]) in order; `parity` flips the read/write buffers on
 // alternate steps.
 template <int Q, typename S, int W, int NS, int MINB>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
-    batch_step_kernel(const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
+    batch_step_kernel(const __grid_constant__ BatchArgs<typename Codec<S>::T, S> P,
+                      const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
                       const BatchTile* __restrict__ tiles, const int32_t* __restrict__ first,
                       int32_t parity) {
-  using Args = StepArgs<typename Codec<S>::T, S>;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ Args s_args;
   const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
   const uint64_t policy = step_smem_init(sm);
   uint32_t g = 0;
@@ -897,19 +904,11 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
 #pragma unroll 1
   for (int t = first[blockIdx.x]; t < t1; ++t) {
     const BatchTile tile = tiles[t];
+    const int dir = (P.cur[tile.member] ^ parity) & 1;
+    const auto& a = P.a[tile.member][dir];
+    if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(a);
     const auto* m = &members[tile.member];
-    const int dir = (m->cur ^ parity) & 1;
-    __syncthreads();  // the previous tile no longer reads s_args
-    {  // all threads copy the member's step arguments, one word each
-      static_assert(sizeof(Args) % 4 == 0 && alignof(Args) >= 4, "word copy");
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(&m->args[dir]);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
-#pragma unroll 1
-      for (int k = threadIdx.x; k < (int)(sizeof(Args) / 4); k += blockDim.x) dst[k] = src[k];
-    }
-    if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(m->args[dir]);
-    __syncthreads();
-    if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, s_args, tile.x0, tile.y0,
+    if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
                                           tile.rows, tile.rev != 0, sm, g, policy))
       return;
   }

@@ -92,7 +92,7 @@ def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
         b.add(c)
     b.add(pkg.Simulation.from_workload(ws[2], storage="fp32"))
     best = b.autotune(steps_per_trial=4)
-    assert best["tile_rows"] in (4, 8, 16, 32, 64) and best["ms_per_step"] > 0
+    assert best["tile_rows"] in (4, 8, 12, 16, 24, 32, 64) and best["ms_per_step"] > 0
     b.step(3)
     assert np.isfinite(a.moments()[0]).all()
     b.close()
@@ -142,4 +142,32 @@ def test_member_reinitialised_between_batch_steps(pkg):
     ref.step(4)
     np.testing.assert_array_equal(sims[1].populations(), ref.populations())
     np.testing.assert_array_equal(sims[0].populations(), _alone(pkg, ws[0], "fp16s", 7))
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+def test_many_members_span_several_launch_chunks(pkg, storage):
+    """70 lattices: three launch chunks of at most 32 members, each chunk on its
+    own stream forked from and joined to the batch stream inside the two-step
+    graph.  Every member still equals its solo run bit for bit, across an odd
+    step count."""
+    ws = [W.droplet_on_wall(nx=24 + 4 * (k % 7), ny=16 + 2 * (k % 5), R=5.0, seed=100 + k,
+                            noise_amp=1e-5, tau=0.7 + 0.01 * k, G_A=0.001 * k) for k in range(70)]
+    want = [_alone(pkg, w, storage, 5) for w in ws]
+    sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
+    b = pkg.Batch()
+    for s in sims:
+        b.add(s)
+    b.step(2)
+    b.step(3)
+    for s, f in zip(sims, want):
+        np.testing.assert_array_equal(s.populations(), f)
+        assert s.steps_done() == 5
+    b.set_tiling(8, 300)       # persistent CTAs shared out over the chunks
+    b.step(2)
+    ref = [pkg.Simulation.from_workload(w, storage=storage) for w in ws[:5]]
+    for r in ref:
+        r.step(7)
+    for s, r in zip(sims[:5], ref):
+        np.testing.assert_array_equal(s.populations(), r.populations())
     b.close()
