@@ -1007,7 +1007,7 @@ template <int Q, typename S> cudaError_t batch_launch(lbm_batch* b, int parity) 
         *reinterpret_cast<const BatchArgs<T, S>*>(ch.args.data()),
         static_cast<const BatchMember<T, S>*>(b->d_members) + ch.base,
         static_cast<const BatchTile*>(b->d_tiles) + ch.tile_off,
-        static_cast<const int32_t*>(b->d_first) + ch.first_off, ch.nctas, parity,
+        static_cast<const int32_t*>(b->d_first) + ch.first_off, ch.nctas, parity, b->ctas > 0,
         multi ? ch.stream : b->stream);
     if (e != cudaSuccess) return e;
   }

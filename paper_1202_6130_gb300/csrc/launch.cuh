@@ -45,7 +45,7 @@ template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
                          const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         cudaStream_t stream);
+                         bool persistent, cudaStream_t stream);
 template <int Q, typename S> int batch_ctas_per_sm();
 
 // Auxiliary kernels (aux.cu).

@@ -51,9 +51,13 @@ template <int Q, typename S>
 static cudaError_t prepare_batch_kernel() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
-  static cudaError_t once = cudaFuncSetAttribute(
-      batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>,
-      cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  static cudaError_t once = [] {
+    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  }();
   return once;
 }
 
@@ -61,13 +65,17 @@ template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
                          const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         cudaStream_t stream) {
+                         bool persistent, cudaStream_t stream) {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   cudaError_t e = prepare_batch_kernel<Q, S>();
   if (e != cudaSuccess) return e;
-  batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>
-      <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
+  if (persistent)
+    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>
+        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
+  else
+    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false>
+        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
   return cudaGetLastError();
 }
 
@@ -77,7 +85,7 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   if (prepare_batch_kernel<Q, S>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB>, Sh::NT, Sh::SMEM) !=
+          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>, Sh::NT, Sh::SMEM) !=
       cudaSuccess)
     return 0;
   return n;
@@ -93,5 +101,5 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   template cudaError_t lbm::launch_batch<Q, S>(                                          \
       const lbm::BatchArgs<lbm::Codec<S>::T, S>&,                                         \
       const lbm::BatchMember<lbm::Codec<S>::T, S>*, const lbm::BatchTile*, const int32_t*, \
-      int, int, cudaStream_t);                                                           \
+      int, int, bool, cudaStream_t);                                                     \
   template int lbm::batch_ctas_per_sm<Q, S>();

@@ -887,10 +887,11 @@ struct BatchTile {
   int32_t member, x0, y0, rows, rev;
 };
 
-// One time step of up to kBatchChunk lattices of a batch.  CTA b marches tiles
-// [first[b], first[b + 1]) in order; `parity` flips the read/write buffers on
-// alternate steps.
-template <int Q, typename S, int W, int NS, int MINB>
+// One time step of up to kBatchChunk lattices of a batch.  With PERSIST, CTA
+// b marches tiles [first[b], first[b + 1]) in order; otherwise CTA b marches
+// tile b (no loop state held across the march).  `parity` flips the
+// read/write buffers on alternate steps.
+template <int Q, typename S, int W, int NS, int MINB, bool PERSIST>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     batch_step_kernel(const __grid_constant__ BatchArgs<typename Codec<S>::T, S> P,
                       const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
@@ -900,17 +901,22 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
   const uint64_t policy = step_smem_init(sm);
   uint32_t g = 0;
-  const int t1 = first[blockIdx.x + 1];
-#pragma unroll 1
-  for (int t = first[blockIdx.x]; t < t1; ++t) {
+  auto march_tile = [&](int t) -> bool {
     const BatchTile tile = tiles[t];
     const int dir = (P.cur[tile.member] ^ parity) & 1;
     const auto& a = P.a[tile.member][dir];
     if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(a);
     const auto* m = &members[tile.member];
-    if (!march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
-                                          tile.rows, tile.rev != 0, sm, g, policy))
-      return;
+    return march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
+                                            tile.rows, tile.rev != 0, sm, g, policy);
+  };
+  if constexpr (PERSIST) {
+    const int t1 = first[blockIdx.x + 1];
+#pragma unroll 1
+    for (int t = first[blockIdx.x]; t < t1; ++t)
+      if (!march_tile(t)) return;
+  } else {
+    march_tile((int)blockIdx.x);
   }
 }
 
