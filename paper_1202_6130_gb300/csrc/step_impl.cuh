@@ -25,8 +25,22 @@ cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
   cudaError_t e;
   if (mode == kModeStep) {
     if ((e = prepare_kernel<Q, S, kModeStep>()) != cudaSuccess) return e;
-    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>
-        <<<grid, Sh::NT, Sh::SMEM, stream>>>(src, flags, a);
+    // Programmatic dependent launch: the step may begin launching while the
+    // previous kernel in the stream drains (the kernel waits before touching
+    // global memory).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(Sh::NT);
+    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, src,
+                           flags, a);
+    if (e != cudaSuccess) return e;
   } else {
     if ((e = prepare_kernel<Q, S, kModeMoments>()) != cudaSuccess) return e;
     step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments, Cfg::MINB>

@@ -856,6 +856,12 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   const uint64_t policy = step_smem_init(sm);
   const int y0 = blockIdx.y * a.tile_rows;
   uint32_t g = 0;
+  // Launched as a programmatic dependent of the previous step: the next step's
+  // CTAs may be scheduled as this grid's last wave drains; every global read
+  // or write (populations, the step counter, the status word) follows the
+  // wait for the previous grid.
+  griddep_launch_dependents();
+  griddep_wait();
   // Every CTA reads the counter in march_any before this launch ends; the
   // word written here is read only by the next step.
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) advance_key<MODE>(a);
