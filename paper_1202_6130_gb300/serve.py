@@ -152,12 +152,17 @@ class Server:
 
     def _stage(self):
         """Creates, on the side stream, the simulations of the waiting requests
-        that fit the budget (strict FIFO: the first that does not fit waits)."""
+        that fit the budget (strict FIFO: the first that does not fit waits).
+        Only requests whose fields are ready are taken, except that an idle
+        GPU waits for the first one."""
         import torch
         while self.queue:
             req = self.queue[0]
             need = footprint_bytes(req.nx, req.ny, self.storage)
             if self.used + need > self.budget:
+                break
+            fut = self.fields[req.id]
+            if not fut.done() and (self.active or self.staged):
                 break
             self.queue.popleft()
             w = self.fields.pop(req.id).result()
