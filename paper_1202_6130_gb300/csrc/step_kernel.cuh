@@ -97,9 +97,13 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int STAGE = NBOX * BOXSLOT + FLAG_SLOT;
   // Nodes per thread: D2Q9 with FP32 arithmetic updates two adjacent columns
   // per thread with packed FP32 instructions; otherwise one.
+  // Nodes per thread: D2Q9 with FP32 arithmetic updates adjacent columns in
+  // packed FP32 pairs, one pair per thread; otherwise one node.  (The paired
+  // march takes any number of pairs per thread; two pairs, i.e. 32-thread
+  // CTAs for 16-bit storage, measured 25% slower than one on GB300.)
   static constexpr int V = (Q == 9 && sizeof(T) == 4) ? 2 : 1;
   static constexpr int NT = W / V;                       // threads per CTA
-  static constexpr int RO = V == 2 ? 2 : R;              // ring column of node 0 (even for V = 2)
+  static constexpr int RO = V >= 2 ? 2 : R;              // ring column of node 0 (even for pairs)
   static constexpr int RING_W = W + 2 * RO;
   static constexpr int RING_H = 2 * R + 2;
   static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
@@ -126,7 +130,7 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   }
   static constexpr Tables kTab = make_tables();
   static_assert(W % 32 == 0 && W >= 64 && CHUNKS <= 256, "strip width");
-  static_assert(NT % 32 == 0 && NT >= 64, "threads per CTA");
+  static_assert(NT % 32 == 0 && NT >= 32, "threads per CTA");
   static_assert(NS >= R + 2, "pipeline depth");
   static_assert(Q % BD == 0, "box depth");
 };
@@ -298,12 +302,10 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       ring_row[tid + Sh::RO] = pseudo_potential<Q, T>(a.phys, rho);
       if constexpr (Sh::kRegs) flag_next = flags_of(stb);
     }
-    {
-      const int lane = tid & 31;
-      if (warp < 2 && lane < R) {
-        const int xl = warp == 0 ? lane - R : W + lane;
-        ring_row[xl + Sh::RO] = psi_at(st, xl);
-      }
+    // The 2R halo columns by the first 2R threads (one warp diverges, not two).
+    if (tid < 2 * R) {
+      const int xl = tid < R ? tid - R : W + tid - R;
+      ring_row[xl + Sh::RO] = psi_at(st, xl);
     }
     __syncthreads();
     if (*s_abort) break;
@@ -483,15 +485,15 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   constexpr int GX = Sh::GX;
   constexpr int GY = Sh::GY;
   constexpr int RO = Sh::RO;
-  static_assert(Sh::V == 2 && Sh::kRegs, "two-node march");
+  constexpr int P = Sh::V / 2;  // node pairs per thread
+  static_assert(Sh::V % 2 == 0 && Sh::kRegs, "paired march");
   unsigned char* const stages = sm.stages;
   uint64_t* const bars = sm.bars;
   T* const ring = sm.ring;
   int* const s_abort = sm.s_abort;
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int xa = 2 * tid;      // first of the thread's two columns, relative to x0
+  const int xa = Sh::V * tid;  // first of the thread's columns, relative to x0
   const int x = x0 + xa;
   const int K = Lr + 2 * R;
   const int ybase = rev ? y0 + Lr + R - 1 : y0 - R;
@@ -499,7 +501,6 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
-  const bool pair_ok = x + 1 < a.nx;  // both nodes exist
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
   const uint32_t key = step_key<S, MODE>(a);
@@ -529,16 +530,17 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     issued = n0;
   }
 
-  // Population I of the thread's two columns: an aligned pair when c_x is even
+  // Population I of the columns of pair p: an aligned pair when c_x is even
   // (one access), else two single loads.
-  auto load_pair = [&](const S* st, auto ic) -> F2 {
+  auto load_pair = [&](const S* st, auto ic, int p) -> F2 {
     constexpr int i = decltype(ic)::value;
     constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
     const F2 wrs = F2::splat(a.phys.shift[i]);
+    const int xc = xa + 2 * p;
     if constexpr ((off & 1) == 0) {
-      return PR::dec(*reinterpret_cast<const typename PR::Raw*>(st + off + xa), wrs);
+      return PR::dec(*reinterpret_cast<const typename PR::Raw*>(st + off + xc), wrs);
     } else {
-      return PR::dec1(st[off + xa], st[off + xa + 1], wrs);
+      return PR::dec1(st[off + xc], st[off + xc + 1], wrs);
     }
   };
   auto psi_at = [&](const S* st, int xl) -> T {  // one node (halo columns)
@@ -552,7 +554,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     return pseudo_potential<Q, T>(a.phys, rho);
   };
 
-  F2 fnext[Q];
+  F2 fnext[P][Q];
   uint32_t flag_next = 0;
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
@@ -563,33 +565,34 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
 
-    F2 f[Q];
+    F2 f[P][Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = fnext[i];
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[p][i] = fnext[p][i];
     const uint32_t flag = flag_next;
 
-    // psi of node row k for both columns, then the halo columns.
+    // psi of node row k for the thread's columns, then the halo columns.
     T* ring_row = ring + (k % Sh::RING_H) * Sh::RING_W;
-    {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
       F2 rho;
       static_for<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const F2 v = load_pair(st, ic);
-        fnext[i] = v;
+        const F2 v = load_pair(st, ic, p);
+        fnext[p][i] = v;
         rho = (i == 0) ? v : rho + v;
       });
       const T pa = pseudo_potential<Q, T>(a.phys, rho.x());
       const T pb = pseudo_potential<Q, T>(a.phys, rho.y());
-      *reinterpret_cast<float2*>(ring_row + RO + xa) = make_float2(pa, pb);
-      flag_next = wall_on ? reinterpret_cast<const uint32_t*>(stb + Sh::NBOX * Sh::BOXSLOT)[tid >> 4]
-                          : 0u;
+      *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = make_float2(pa, pb);
     }
-    {
-      const int lane = tid & 31;
-      if (warp < 2 && lane < R) {
-        const int xl = warp == 0 ? lane - R : W + lane;
-        ring_row[xl + RO] = psi_at(st, xl);
-      }
+    // the thread's columns lie in one 32-column flag chunk
+    flag_next = wall_on ? reinterpret_cast<const uint32_t*>(stb + Sh::NBOX * Sh::BOXSLOT)[xa >> 5]
+                        : 0u;
+    if (tid < 2 * R) {
+      const int xl = tid < R ? tid - R : W + tid - R;
+      ring_row[xl + RO] = psi_at(st, xl);
     }
     __syncthreads();
     if (*s_abort) break;
@@ -605,209 +608,216 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     if (k >= 2 * R) {
       const int ko = k - R;
       const int yo = ybase + ds * ko;
-      // rho and j of both nodes, table order.
-      F2 rho = f[0], jx = f[1] - f[3], jy = f[2] - f[4];
-      {
-        rho += f[1];
-        rho += f[2];
-        rho += f[3];
-        rho += f[4];
-        rho += f[5];
-        rho += f[6];
-        rho += f[7];
-        rho += f[8];
-        jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-        jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-      }
-      const F2 inv_rho(T(1) / rho.x(), T(1) / rho.y());
-      const F2 ux = jx * inv_rho;
-      const F2 uy = jy * inv_rho;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int xp = x + 2 * p;           // first column of pair p
+        const bool pair_ok = xp + 1 < a.nx;  // both nodes exist
+        F2 (&f_)[Q] = f[p];
+        // rho and j of both nodes, table order.
+        F2 rho = f_[0], jx = f_[1] - f_[3], jy = f_[2] - f_[4];
+        {
+          rho += f_[1];
+          rho += f_[2];
+          rho += f_[3];
+          rho += f_[4];
+          rho += f_[5];
+          rho += f_[6];
+          rho += f_[7];
+          rho += f_[8];
+          jx = f_[1] - f_[3] + f_[5] - f_[6] - f_[7] + f_[8];
+          jy = f_[2] - f_[4] + f_[5] + f_[6] - f_[7] - f_[8];
+        }
+        const F2 inv_rho(T(1) / rho.x(), T(1) / rho.y());
+        const F2 ux = jx * inv_rho;
+        const F2 uy = jy * inv_rho;
 
-      // Neighbour psi: three aligned pairs per ring row cover columns xa-2 .. xa+3.
-      F2 sfx = F2::splat(0.f), sfy = F2::splat(0.f), psi_c;
-      static_for<0, 3>([&](auto rc) {
-        constexpr int cy = decltype(rc)::value - 1;
-        const T* row = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa;
-        const float2 A = *reinterpret_cast<const float2*>(row - 2);
-        const float2 B = *reinterpret_cast<const float2*>(row);
-        const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
-        const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
-        if constexpr (cy == 0) {
-          psi_c = p0;
-          const F2 d = pp - pm;                       // (1,0) and (-1,0)
-          sfx = fma2(F2::splat(T(L::w(1))), d, sfx);
-        } else {
-          // (0,cy): weight w_axis; (+-1, cy): weight w_diag
-          const F2 axis = p0 * F2::splat(T(L::w(2)));
-          const F2 dsum = (pp + pm) * F2::splat(T(L::w(5)));
-          const F2 ddif = (pp - pm) * F2::splat(T(L::w(5)));
-          if constexpr (cy > 0) {
-            sfy = sfy + axis + dsum;
+        // Neighbour psi: three aligned pairs per ring row cover the pair's
+        // columns and one more on either side.
+        F2 sfx = F2::splat(0.f), sfy = F2::splat(0.f), psi_c;
+        static_for<0, 3>([&](auto rc) {
+          constexpr int cy = decltype(rc)::value - 1;
+          const T* row = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa + 2 * p;
+          const float2 A = *reinterpret_cast<const float2*>(row - 2);
+          const float2 B = *reinterpret_cast<const float2*>(row);
+          const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
+          const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
+          if constexpr (cy == 0) {
+            psi_c = p0;
+            const F2 d = pp - pm;                       // (1,0) and (-1,0)
+            sfx = fma2(F2::splat(T(L::w(1))), d, sfx);
           } else {
-            sfy = sfy - axis - dsum;
-          }
-          sfx = sfx + ddif;
-        }
-      });
-
-      // Force: F_FF, then the wall terms on flagged chunks, then body force.
-      const F2 mg = F2::splat(-a.phys.G) * psi_c;
-      const F2 ffx = mg * sfx, ffy = mg * sfy;
-      F2 Fx = ffx, Fy = ffy;
-      if (flag != 0u) {
-        T phe[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0}, wx[2] = {0, 0}, wy[2] = {0, 0};
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          if (x + e < a.nx) {
-            const int64_t n = (int64_t)yo * a.nx + x + e;
-            phe[e] = a.wall.phie[n];
-            Sx[e] = a.wall.sx[n];
-            Sy[e] = a.wall.sy[n];
-            if (a.wall.uwx) {
-              wx[e] = a.wall.uwx[n];
-              wy[e] = a.wall.uwy[n];
-            }
-          }
-        }
-        const F2 rp = rho * F2(phe[0], phe[1]);
-        const F2 dfx = rp * (F2(wx[0], wx[1]) - ux - ffx * inv_rho);
-        const F2 dfy = rp * (F2(wy[0], wy[1]) - uy - ffy * inv_rho);
-        Fx = (ffx + rho * F2(Sx[0], Sx[1])) + dfx;
-        Fy = (ffy + rho * F2(Sy[0], Sy[1])) + dfy;
-      }
-      Fx += F2::splat(a.phys.bfx);
-      Fy += F2::splat(a.phys.bfy);
-
-      if (x < a.nx) {
-        if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
-          atomicOr(a.status, kStatusNonFinite);
-        if constexpr (MODE == kModeStep) {
-          const F2 usx = fma2(Fx, inv_rho, ux);
-          const F2 usy = fma2(Fy, inv_rho, uy);
-          // EDM-BGK in pair form (see node_collide), packed over the two nodes.
-          const F2 gg = F2::splat(a.phys.one_m_omega);
-          const F2 ax = usx - gg * ux, ay = usy - gg * uy;
-          const F2 Bt = (usx * usx + usy * usy - gg * (ux * ux + uy * uy)) *
-                        F2::splat(T(E::inv_2theta));
-          const F2 wB = F2::splat(a.phys.omega) - Bt;
-          if (a.phys.project) {
-            // rare path: per node
-            T fa[Q], fb[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              fa[i] = f[i].x();
-              fb[i] = f[i].y();
-            }
-            project<Q, T>(fa, rho.x(), jx.x(), jy.x());
-            project<Q, T>(fb, rho.y(), jx.y(), jy.y());
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = F2(fa[i], fb[i]);
-          }
-          static_for<0, Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr int j = opposite<Q>(i);
-            if constexpr (i == L::REST) {
-              f[i] = fma2(gg, f[i], F2::splat(T(L::w(i))) * rho * wB);
-            } else if constexpr (i < j) {
-              const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
-              const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
-              const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax, ay);
-              const F2 wr = F2::splat(T(L::w(i))) * rho;
-              const F2 t = cs * cs - gg * (cu * cu);
-              const F2 Sp = wr * fma2(t, F2::splat(T(E::inv_2theta2)), wB);
-              const F2 Ap = wr * (ca * F2::splat(T(E::inv_theta)));
-              const F2 fi = fma2(gg, f[i], Sp + Ap);
-              const F2 fj = fma2(gg, f[j], Sp - Ap);
-              f[i] = fi;
-              f[j] = fj;
-            }
-          });
-          {  // mass closure of the rest population (FP32 arithmetic)
-            F2 moving = f[1];
-            moving += f[2];
-            moving += f[3];
-            moving += f[4];
-            moving += f[5];
-            moving += f[6];
-            moving += f[7];
-            moving += f[8];
-            f[0] = rho - moving;
-          }
-          // Encode both nodes once (stochastic rounding: bits from the node pair
-          // and the step), then the primary store plus periodic images.
-          typename PR::Raw raw[Q];
-          if constexpr (C::kShifted) {
-            if (a.stochastic) {
-              const uint32_t h = sr_hash((uint32_t)x, (uint32_t)yo, key);
-              static_for<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                raw[i] = PR::enc_sr(f[i], F2::splat(a.phys.enc_add[i]), h * sr_multiplier(i));
-              });
+            // (0,cy): weight w_axis; (+-1, cy): weight w_diag
+            const F2 axis = p0 * F2::splat(T(L::w(2)));
+            const F2 dsum = (pp + pm) * F2::splat(T(L::w(5)));
+            const F2 ddif = (pp - pm) * F2::splat(T(L::w(5)));
+            if constexpr (cy > 0) {
+              sfy = sfy + axis + dsum;
             } else {
-              static_for<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                raw[i] = PR::enc(f[i], F2::splat(a.phys.enc_add[i]));
-              });
+              sfy = sfy - axis - dsum;
             }
-          } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) raw[i] = PR::enc(f[i], F2::splat(0.f));
+            sfx = sfx + ddif;
           }
-          S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
-          if (pair_ok) {
-            static_for<0, Q>([&](auto ic) {
-              constexpr int i = decltype(ic)::value;
-              *reinterpret_cast<typename PR::Raw*>(out + Planes<Q>::template plane<i> * a.plane) =
-                  raw[i];
-            });
-          } else {
-            static_for<0, Q>([&](auto ic) {
-              constexpr int i = decltype(ic)::value;
-              out[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], 0);
-            });
-          }
-          const bool edge = (strip_edge && (x < GX || x + 1 >= a.nx - GX)) || yo < GY ||
-                            yo >= a.ny - GY;
-          if (edge) {
-#pragma unroll 1
-            for (int e = 0; e < 2; ++e) {
-              const int xn = x + e;
-              if (xn >= a.nx) break;
-              int xs = xn;
-              while (xs - a.nx >= -GX) xs -= a.nx;
-              int ya = yo;
-              while (ya - a.ny >= -GY) ya -= a.ny;
-              for (int ym = ya; ym < a.ny + GY; ym += a.ny) {
-                for (int xm = xs; xm < a.nx + GX; xm += a.nx) {
-                  if (xm == xn && ym == yo) continue;
-                  S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
-                  static_for<0, Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    o2[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], e);
-                  });
-                }
+        });
+
+        // Force: F_FF, then the wall terms on flagged chunks, then body force.
+        const F2 mg = F2::splat(-a.phys.G) * psi_c;
+        const F2 ffx = mg * sfx, ffy = mg * sfy;
+        F2 Fx = ffx, Fy = ffy;
+        if (flag != 0u) {
+          T phe[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0}, wx[2] = {0, 0}, wy[2] = {0, 0};
+  #pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            if (xp + e < a.nx) {
+              const int64_t n = (int64_t)yo * a.nx + xp + e;
+              phe[e] = a.wall.phie[n];
+              Sx[e] = a.wall.sx[n];
+              Sy[e] = a.wall.sy[n];
+              if (a.wall.uwx) {
+                wx[e] = a.wall.uwx[n];
+                wy[e] = a.wall.uwy[n];
               }
             }
           }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            if (x + e >= a.nx) break;
-            const int64_t n = (int64_t)yo * a.nx + x + e;
-            const double r = e == 0 ? rho.x() : rho.y();
-            const double px = (double)(e == 0 ? jx.x() : jx.y()) + 0.5 * (double)(e == 0 ? Fx.x() : Fx.y());
-            const double py = (double)(e == 0 ? jy.x() : jy.y()) + 0.5 * (double)(e == 0 ? Fy.x() : Fy.y());
-            a.out_rho[n] = r;
-            if (a.momentum) {
-              a.out_ux[n] = px;
-              a.out_uy[n] = py;
+          const F2 rp = rho * F2(phe[0], phe[1]);
+          const F2 dfx = rp * (F2(wx[0], wx[1]) - ux - ffx * inv_rho);
+          const F2 dfy = rp * (F2(wy[0], wy[1]) - uy - ffy * inv_rho);
+          Fx = (ffx + rho * F2(Sx[0], Sx[1])) + dfx;
+          Fy = (ffy + rho * F2(Sy[0], Sy[1])) + dfy;
+        }
+        Fx += F2::splat(a.phys.bfx);
+        Fy += F2::splat(a.phys.bfy);
+
+        if (xp < a.nx) {
+          if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
+            atomicOr(a.status, kStatusNonFinite);
+          if constexpr (MODE == kModeStep) {
+            const F2 usx = fma2(Fx, inv_rho, ux);
+            const F2 usy = fma2(Fy, inv_rho, uy);
+            // EDM-BGK in pair form (see node_collide), packed over the two nodes.
+            const F2 gg = F2::splat(a.phys.one_m_omega);
+            const F2 ax = usx - gg * ux, ay = usy - gg * uy;
+            const F2 Bt = (usx * usx + usy * usy - gg * (ux * ux + uy * uy)) *
+                          F2::splat(T(E::inv_2theta));
+            const F2 wB = F2::splat(a.phys.omega) - Bt;
+            if (a.phys.project) {
+              // rare path: per node
+              T fa[Q], fb[Q];
+  #pragma unroll
+              for (int i = 0; i < Q; ++i) {
+                fa[i] = f_[i].x();
+                fb[i] = f_[i].y();
+              }
+              project<Q, T>(fa, rho.x(), jx.x(), jy.x());
+              project<Q, T>(fb, rho.y(), jx.y(), jy.y());
+  #pragma unroll
+              for (int i = 0; i < Q; ++i) f_[i] = F2(fa[i], fb[i]);
+            }
+            static_for<0, Q>([&](auto ic) {
+              constexpr int i = decltype(ic)::value;
+              constexpr int j = opposite<Q>(i);
+              if constexpr (i == L::REST) {
+                f_[i] = fma2(gg, f_[i], F2::splat(T(L::w(i))) * rho * wB);
+              } else if constexpr (i < j) {
+                const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
+                const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
+                const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax, ay);
+                const F2 wr = F2::splat(T(L::w(i))) * rho;
+                const F2 t = cs * cs - gg * (cu * cu);
+                const F2 Sp = wr * fma2(t, F2::splat(T(E::inv_2theta2)), wB);
+                const F2 Ap = wr * (ca * F2::splat(T(E::inv_theta)));
+                const F2 fi = fma2(gg, f_[i], Sp + Ap);
+                const F2 fj = fma2(gg, f_[j], Sp - Ap);
+                f_[i] = fi;
+                f_[j] = fj;
+              }
+            });
+            {  // mass closure of the rest population (FP32 arithmetic)
+              F2 moving = f_[1];
+              moving += f_[2];
+              moving += f_[3];
+              moving += f_[4];
+              moving += f_[5];
+              moving += f_[6];
+              moving += f_[7];
+              moving += f_[8];
+              f_[0] = rho - moving;
+            }
+            // Encode both nodes once (stochastic rounding: bits from the node pair
+            // and the step), then the primary store plus periodic images.
+            typename PR::Raw raw[Q];
+            if constexpr (C::kShifted) {
+              if (a.stochastic) {
+                const uint32_t h = sr_hash((uint32_t)xp, (uint32_t)yo, key);
+                static_for<0, Q>([&](auto ic) {
+                  constexpr int i = decltype(ic)::value;
+                  raw[i] = PR::enc_sr(f_[i], F2::splat(a.phys.enc_add[i]), h * sr_multiplier(i));
+                });
+              } else {
+                static_for<0, Q>([&](auto ic) {
+                  constexpr int i = decltype(ic)::value;
+                  raw[i] = PR::enc(f_[i], F2::splat(a.phys.enc_add[i]));
+                });
+              }
             } else {
-              a.out_ux[n] = px / r;
-              a.out_uy[n] = py / r;
+  #pragma unroll
+              for (int i = 0; i < Q; ++i) raw[i] = PR::enc(f_[i], F2::splat(0.f));
+            }
+            S* out = a.fout + (int64_t)(yo + GY) * a.pitch + xp + GX;
+            if (pair_ok) {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                *reinterpret_cast<typename PR::Raw*>(out + Planes<Q>::template plane<i> * a.plane) =
+                    raw[i];
+              });
+            } else {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                out[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], 0);
+              });
+            }
+            const bool edge = (strip_edge && (xp < GX || xp + 1 >= a.nx - GX)) || yo < GY ||
+                              yo >= a.ny - GY;
+            if (edge) {
+  #pragma unroll 1
+              for (int e = 0; e < 2; ++e) {
+                const int xn = xp + e;
+                if (xn >= a.nx) break;
+                int xs = xn;
+                while (xs - a.nx >= -GX) xs -= a.nx;
+                int ya = yo;
+                while (ya - a.ny >= -GY) ya -= a.ny;
+                for (int ym = ya; ym < a.ny + GY; ym += a.ny) {
+                  for (int xm = xs; xm < a.nx + GX; xm += a.nx) {
+                    if (xm == xn && ym == yo) continue;
+                    S* o2 = a.fout + (int64_t)(ym + GY) * a.pitch + xm + GX;
+                    static_for<0, Q>([&](auto ic) {
+                      constexpr int i = decltype(ic)::value;
+                      o2[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], e);
+                    });
+                  }
+                }
+              }
+            }
+          } else {
+  #pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              if (xp + e >= a.nx) break;
+              const int64_t n = (int64_t)yo * a.nx + xp + e;
+              const double r = e == 0 ? rho.x() : rho.y();
+              const double px = (double)(e == 0 ? jx.x() : jx.y()) + 0.5 * (double)(e == 0 ? Fx.x() : Fx.y());
+              const double py = (double)(e == 0 ? jy.x() : jy.y()) + 0.5 * (double)(e == 0 ? Fy.x() : Fy.y());
+              a.out_rho[n] = r;
+              if (a.momentum) {
+                a.out_ux[n] = px;
+                a.out_uy[n] = py;
+              } else {
+                a.out_ux[n] = px / r;
+                a.out_uy[n] = py / r;
+              }
             }
           }
         }
-      }
+      }  // pairs
     }
     if (++s == NS) {
       s = 0;
@@ -836,7 +846,7 @@ __device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensor
                                           const Args& a, int x0, int y0, int Lr, bool rev,
                                           const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                           uint64_t policy) {
-  if constexpr (StepShape<Q, S, W, NS>::V == 2)
+  if constexpr (StepShape<Q, S, W, NS>::V >= 2)
     return march_segment_v2<S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g);
   else
     return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g, policy);
