@@ -627,7 +627,8 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
           jx = f_[1] - f_[3] + f_[5] - f_[6] - f_[7] + f_[8];
           jy = f_[2] - f_[4] + f_[5] + f_[6] - f_[7] - f_[8];
         }
-        const F2 inv_rho(T(1) / rho.x(), T(1) / rho.y());
+        // correctly rounded reciprocal: the same value as 1 / rho
+        const F2 inv_rho(__frcp_rn(rho.x()), __frcp_rn(rho.y()));
         const F2 ux = jx * inv_rho;
         const F2 uy = jy * inv_rho;
 
