@@ -70,7 +70,8 @@ def rel_errors(g, o):
     rho_g, ux_g, uy_g = g
     rho_o, ux_o, uy_o = o
     e_rho = float(np.max(np.abs(rho_g - rho_o) / np.abs(rho_o)))
-    umax = max(float(np.max(np.abs(ux_o))), float(np.max(np.abs(uy_o))), 1e-300)
+    # velocity scale: the oracle's maximum, floored at 1e-3 for states at rest
+    umax = max(float(np.max(np.abs(ux_o))), float(np.max(np.abs(uy_o))), 1e-3)
     e_u_abs = max(float(np.max(np.abs(ux_g - ux_o))), float(np.max(np.abs(uy_g - uy_o))))
     return e_rho, e_u_abs / umax, e_u_abs
 
@@ -161,6 +162,9 @@ CASES = [
     dict(nx=8, ny=8, tile_rows=3),
     dict(nx=1, ny=16, tile_rows=4),
     dict(nx=130, ny=3, tile_rows=1),
+    dict(nx=40, ny=1, tile_rows=0),
+    dict(nx=1, ny=1, tile_rows=0),
+    dict(nx=5, ny=2, lattice=21, tile_rows=1),
     dict(nx=257, ny=40, tile_rows=0, uwall=True, body=(1e-5, -2e-6)),
     dict(nx=33, ny=29, lattice=21, tile_rows=4),
     dict(nx=140, ny=23, lattice=21, tile_rows=0, uwall=True, body=(3e-6, 0.0)),
@@ -180,6 +184,27 @@ def test_fp64_ragged_and_multi_tile_match_oracle(pkg, case):
     sim.step(steps)
     e_rho, e_u, _ = rel_errors(sim.moments(), (rho, ux, uy))
     assert e_rho <= 1e-12 and e_u <= 1e-12, (e_rho, e_u)
+
+
+PAIRED_CASES = [dict(nx=67, ny=35, tile_rows=5), dict(nx=1, ny=16, tile_rows=4),
+                dict(nx=3, ny=1, tile_rows=0), dict(nx=129, ny=7, tile_rows=3, uwall=True,
+                                                    body=(1e-5, 0.0))]
+
+
+@pytest.mark.parametrize("case", PAIRED_CASES, ids=lambda c: "x".join(map(str, (c["nx"], c["ny"]))))
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16s", 2e-2)])
+def test_paired_path_ragged_sizes_match_oracle(pkg, case, storage, tol):
+    """The two-nodes-per-thread path on odd widths (a lone last column), a
+    one-column and a one-row lattice, many tiles: FP32 within 1e-5 of the
+    oracle after 40 steps, 16-bit storage within its rounding."""
+    case = dict(case)
+    tr = case.pop("tile_rows")
+    w = _small_case(**case)
+    _, rho, ux, uy = run_oracle(w, 40)
+    sim = make_sim(pkg, w, storage, tile_rows=tr)
+    sim.step(40)
+    e_rho, e_u, _ = rel_errors(sim.moments(), (rho, ux, uy))
+    assert e_rho <= tol and e_u <= tol * 10, (e_rho, e_u)
 
 
 @pytest.mark.parametrize("lattice", [9, 21])
