@@ -14,15 +14,19 @@
 // holds post-collision values f_i^post(x) at the emitting node; the next step
 // pulls f_i(x) = f_i^post(x - c_i).
 //
-// Schedule.  A CTA of W threads owns a strip of W columns and a segment of L
-// rows, and marches down the segment one node row at a time.  Each row's Q
-// source rows (one per population, shifted by -c_y) and the row's wall flags
-// arrive by TMA in one of NS shared-memory stages, several rows ahead of use.
-// psi is computed once per node (plus R halo nodes on each side of the strip)
-// into a ring of 2R+2 rows; the collision of row k - R then reads its
-// neighbours' psi from the ring.  The extra ring row lets one barrier per row
-// order both the ring and the stage reuse.  psi never touches HBM; the only
-// redundant traffic is the 2R halo columns and rows of each strip segment.
+// Schedule.  A CTA owns a strip of W columns and a segment of L rows (one
+// thread per column, or per pair of columns with packed FP32 arithmetic) and
+// marches through the segment one node row at a time, downwards for even
+// segments and upwards for odd ones, so that vertically adjacent segments pull
+// the rows they share at about the same time (the second pull hits in L2).
+// Each row's Q source rows (one per population, shifted by -c_y) and the row's
+// wall flags arrive by TMA in one of NS shared-memory stages, several rows
+// ahead of use.  psi is computed once per node (plus R halo nodes on each side
+// of the strip, by the first 2R threads) into a ring of 2R+2 rows; the
+// collision of row k - R then reads its neighbours' psi from the ring.  The
+// extra ring row lets one barrier per row order both the ring and the stage
+// reuse.  psi never touches HBM; the redundant work is the 2R halo columns and
+// rows of each strip segment.
 #pragma once
 
 #include <cuda.h>
