@@ -184,6 +184,16 @@ template <typename T> struct WallFields {
 template <typename T> __device__ __forceinline__ T t_exp(T v);
 template <> __device__ __forceinline__ double t_exp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float t_exp<float>(float v) { return expf(v); }
+// 1 / rho.  FP64 divides exactly (quotients then divide, like the oracle);
+// FP32 arithmetic takes the hardware reciprocal (PTX rcp.approx.ftz.f32, at
+// most 1 ulp from the correctly rounded value), which every FP32 kernel shares.
+template <typename T> __device__ __forceinline__ T t_rcp(T v);
+template <> __device__ __forceinline__ double t_rcp<double>(double v) { return 1.0 / v; }
+template <> __device__ __forceinline__ float t_rcp<float>(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 template <typename T> __device__ __forceinline__ T t_fma(T a, T b, T c);
 template <> __device__ __forceinline__ double t_fma<double>(double a, double b, double c) {
   return fma(a, b, c);

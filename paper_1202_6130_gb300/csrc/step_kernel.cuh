@@ -160,8 +160,8 @@ template <int Q, typename S, int W, int NS> struct StepSmem {
   }
 };
 
-// Roles: the first lane of the last warp issues the TMA copies; the first
-// lanes of warps 0 and 1 form the left and right halo psi.
+// Roles: the first lane of the last warp issues the TMA copies; the first 2R
+// threads (all in warp 0) form the psi of the R halo columns on either side.
 template <int NT> constexpr int kIssuer = NT - 32;
 
 // Initialises the stage barriers (once per CTA) and returns the L2 policy the
@@ -336,7 +336,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       }
       T rho, jx, jy;
       node_moments<Q, T>(f, rho, jx, jy);
-      const T inv_rho = T(1) / rho;
+      const T inv_rho = t_rcp<T>(rho);
       const T ux = div_rho<T>(jx, rho, inv_rho);
       const T uy = div_rho<T>(jy, rho, inv_rho);
 
@@ -559,6 +559,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
   };
 
   F2 fnext[P][Q];
+  F2 rho_next[P];  // rho of those populations, summed once in table order
   uint32_t flag_next = 0;
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
@@ -574,6 +575,9 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     for (int p = 0; p < P; ++p)
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[p][i] = fnext[p][i];
+    F2 rho_cur[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) rho_cur[p] = rho_next[p];
     const uint32_t flag = flag_next;
 
     // psi of node row k for the thread's columns, then the halo columns.
@@ -590,6 +594,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
       const T pa = pseudo_potential<Q, T>(a.phys, rho.x());
       const T pb = pseudo_potential<Q, T>(a.phys, rho.y());
       *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = make_float2(pa, pb);
+      rho_next[p] = rho;
     }
     // the thread's columns lie in one 32-column flag chunk
     flag_next = wall_on ? reinterpret_cast<const uint32_t*>(stb + Sh::NBOX * Sh::BOXSLOT)[xa >> 5]
@@ -617,22 +622,14 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
         const int xp = x + 2 * p;           // first column of pair p
         const bool pair_ok = xp + 1 < a.nx;  // both nodes exist
         F2 (&f_)[Q] = f[p];
-        // rho and j of both nodes, table order.
-        F2 rho = f_[0], jx = f_[1] - f_[3], jy = f_[2] - f_[4];
-        {
-          rho += f_[1];
-          rho += f_[2];
-          rho += f_[3];
-          rho += f_[4];
-          rho += f_[5];
-          rho += f_[6];
-          rho += f_[7];
-          rho += f_[8];
-          jx = f_[1] - f_[3] + f_[5] - f_[6] - f_[7] + f_[8];
-          jy = f_[2] - f_[4] + f_[5] + f_[6] - f_[7] - f_[8];
-        }
-        // correctly rounded reciprocal: the same value as 1 / rho
-        const F2 inv_rho(__frcp_rn(rho.x()), __frcp_rn(rho.y()));
+        // rho of both nodes carried from the psi pass (table order); j with
+        // the diagonal differences f5 - f7 and f8 - f6 shared by its two
+        // components.
+        const F2 rho = rho_cur[p];
+        const F2 d57 = f_[5] - f_[7], d86 = f_[8] - f_[6];
+        const F2 jx = ((f_[1] - f_[3]) + d57) + d86;
+        const F2 jy = ((f_[2] - f_[4]) + d57) - d86;
+        const F2 inv_rho(t_rcp<float>(rho.x()), t_rcp<float>(rho.y()));
         const F2 ux = jx * inv_rho;
         const F2 uy = jy * inv_rho;
 
@@ -648,27 +645,21 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
           const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
           if constexpr (cy == 0) {
             psi_c = p0;
-            const F2 d = pp - pm;                       // (1,0) and (-1,0)
-            sfx = fma2(F2::splat(T(L::w(1))), d, sfx);
+            sfx = fma2(pp - pm, F2::splat(T(L::w(1))), sfx);  // (1,0) and (-1,0)
           } else {
             // (0,cy): weight w_axis; (+-1, cy): weight w_diag
-            const F2 axis = p0 * F2::splat(T(L::w(2)));
-            const F2 dsum = (pp + pm) * F2::splat(T(L::w(5)));
-            const F2 ddif = (pp - pm) * F2::splat(T(L::w(5)));
-            if constexpr (cy > 0) {
-              sfy = sfy + axis + dsum;
-            } else {
-              sfy = sfy - axis - dsum;
-            }
-            sfx = sfx + ddif;
+            constexpr T sg = cy > 0 ? T(1) : T(-1);
+            sfy = fma2(p0, F2::splat(sg * T(L::w(2))), sfy);
+            sfy = fma2(pp + pm, F2::splat(sg * T(L::w(5))), sfy);
+            sfx = fma2(pp - pm, F2::splat(T(L::w(5))), sfx);
           }
         });
 
         // Force: F_FF, then the wall terms on flagged chunks, then body force.
         const F2 mg = F2::splat(-a.phys.G) * psi_c;
-        const F2 ffx = mg * sfx, ffy = mg * sfy;
-        F2 Fx = ffx, Fy = ffy;
+        F2 Fx, Fy;
         if (flag != 0u) {
+          const F2 ffx = mg * sfx, ffy = mg * sfy;
           T phe[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0}, wx[2] = {0, 0}, wy[2] = {0, 0};
   #pragma unroll
           for (int e = 0; e < 2; ++e) {
@@ -686,11 +677,12 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
           const F2 rp = rho * F2(phe[0], phe[1]);
           const F2 dfx = rp * (F2(wx[0], wx[1]) - ux - ffx * inv_rho);
           const F2 dfy = rp * (F2(wy[0], wy[1]) - uy - ffy * inv_rho);
-          Fx = (ffx + rho * F2(Sx[0], Sx[1])) + dfx;
-          Fy = (ffy + rho * F2(Sy[0], Sy[1])) + dfy;
+          Fx = ((ffx + rho * F2(Sx[0], Sx[1])) + dfx) + F2::splat(a.phys.bfx);
+          Fy = ((ffy + rho * F2(Sy[0], Sy[1])) + dfy) + F2::splat(a.phys.bfy);
+        } else {
+          Fx = fma2(mg, sfx, F2::splat(a.phys.bfx));
+          Fy = fma2(mg, sfy, F2::splat(a.phys.bfy));
         }
-        Fx += F2::splat(a.phys.bfx);
-        Fy += F2::splat(a.phys.bfy);
 
         if (xp < a.nx) {
           if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
@@ -698,12 +690,16 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
           if constexpr (MODE == kModeStep) {
             const F2 usx = fma2(Fx, inv_rho, ux);
             const F2 usy = fma2(Fy, inv_rho, uy);
-            // EDM-BGK in pair form (see node_collide), packed over the two nodes.
-            const F2 gg = F2::splat(a.phys.one_m_omega);
-            const F2 ax = usx - gg * ux, ay = usy - gg * uy;
-            const F2 Bt = (usx * usx + usy * usy - gg * (ux * ux + uy * uy)) *
-                          F2::splat(T(E::inv_2theta));
-            const F2 wB = F2::splat(a.phys.omega) - Bt;
+            // EDM-BGK in pair form (see node_collide), packed over the two nodes
+            // and written as fused multiply-adds: with ca = c.(u* - g u) / theta
+            // and sb = omega - B + ((c.u*)^2 - g (c.u)^2) / (2 theta^2),
+            // f_post(+-c) = g f(+-c) + w rho (sb +- ca).
+            const F2 gg = F2::splat(a.phys.one_m_omega), ngg = F2::splat(-a.phys.one_m_omega);
+            const F2 ax3 = fma2(ngg, ux, usx) * F2::splat(T(E::inv_theta));
+            const F2 ay3 = fma2(ngg, uy, usy) * F2::splat(T(E::inv_theta));
+            const F2 us2 = fma2(usy, usy, usx * usx), u2 = fma2(uy, uy, ux * ux);
+            const F2 wB = fma2(fma2(ngg, u2, us2), F2::splat(-T(E::inv_2theta)),
+                               F2::splat(a.phys.omega));
             if (a.phys.project) {
               // rare path: per node
               T fa[Q], fb[Q];
@@ -720,18 +716,16 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
             static_for<0, Q>([&](auto ic) {
               constexpr int i = decltype(ic)::value;
               constexpr int j = opposite<Q>(i);
-              if constexpr (i == L::REST) {
-                f_[i] = fma2(gg, f_[i], F2::splat(T(L::w(i))) * rho * wB);
-              } else if constexpr (i < j) {
+              // The rest population comes from the mass closure below.
+              if constexpr (i != L::REST && i < j) {
                 const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
                 const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
-                const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax, ay);
+                const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax3, ay3);
                 const F2 wr = F2::splat(T(L::w(i))) * rho;
-                const F2 t = cs * cs - gg * (cu * cu);
-                const F2 Sp = wr * fma2(t, F2::splat(T(E::inv_2theta2)), wB);
-                const F2 Ap = wr * (ca * F2::splat(T(E::inv_theta)));
-                const F2 fi = fma2(gg, f_[i], Sp + Ap);
-                const F2 fj = fma2(gg, f_[j], Sp - Ap);
+                const F2 t = fma2(ngg, cu * cu, cs * cs);
+                const F2 sb = fma2(t, F2::splat(T(E::inv_2theta2)), wB);
+                const F2 fi = fma2(gg, f_[i], wr * (sb + ca));
+                const F2 fj = fma2(gg, f_[j], wr * (sb - ca));
                 f_[i] = fi;
                 f_[j] = fj;
               }
