@@ -41,6 +41,10 @@ WORKLOAD = ("8192x4096 D2Q9 pseudo-potential wetting LB, 64 drops R~U[40,120] se
             "core 0.1 / tail 0.05")
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16", "bf16s": "bf16"}
 BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
+def workload_name(nx: int, ny: int, lattice: int) -> str:
+    return WORKLOAD.replace("8192x4096", f"{nx}x{ny}").replace("D2Q9", f"D2Q{lattice}")
+
+
 KERNEL_SOURCES = ["step_kernel.cuh", "node.cuh", "f2.cuh", "tma.cuh", "lattice.cuh", "launch.cuh",
                   "step_impl.cuh", "engine.cu"]
 
@@ -68,10 +72,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(storage: str):
+def ncu_traffic(storage: str, lattice: int = 9):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     if it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", f"step_{storage}_d2q9_8192x4096.txt")
+    path = os.path.join(ROOT, "profiles", f"step_{storage}_d2q{lattice}_8192x4096.txt")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -183,7 +187,7 @@ class OracleBand:
     """The FP64 oracle on rows [0, rows) of the workload: a periodic band of the
     full 8192-wide lattice with its wall (the sample the CPU legs time)."""
 
-    def __init__(self, rows: int):
+    def __init__(self, rows: int, lattice: int = 9):
         import workloads as W
         from oracle import lbm_oracle as O
         self.O = O
@@ -191,7 +195,7 @@ class OracleBand:
         T = 3.0 + 1.5 * np.sin(2.0 * np.pi * 8.0 * np.arange(NX) / NX)
         rho = W.droplet_density(NX, rows, w.meta["centers"], w.meta["radii"], 2.0, 0.15, 2.0)
         phi, pr, pa = W.wall_core_tail(W.wall_distance_slab(NX, rows), T[None, :])
-        self.p = O.Params(lattice=O.D2Q9, tau=1.0, G=-5.5)
+        self.p = O.Params(lattice=O.LATTICES[lattice], tau=1.0, G=-5.5)
         self.wall = O.Wall(phi, pr, pa, 0.1, 0.05, 1.0)
         z = np.zeros_like(rho)
         self.f = O.initial_populations(self.p, rho, z, z)
@@ -205,15 +209,16 @@ class OracleBand:
         return time.perf_counter() - t0
 
 
-def cpu_baseline(target_s: float = 15.0):
+def cpu_baseline(target_s: float = 15.0, lattice: int = 9):
     rows = 256
-    band = OracleBand(rows)
+    band = OracleBand(rows, lattice)
     dt1 = band.step(1)
     steps = max(1, int(target_s / max(dt1, 1e-3)))
     dt = band.step(steps)
     return {"value": band.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, rows 0..{rows - 1} of the 8192-wide workload as a "
-                      f"periodic {NX}x{rows} band with its wall, {steps} steps, one thread"}
+            "sample": f"FP64 numpy oracle (D2Q{lattice}), rows 0..{rows - 1} of the 8192-wide "
+                      f"workload as a periodic {NX}x{rows} band with its wall, {steps} steps, "
+                      "one thread"}
 
 
 def run_reference(args, world, rank):
@@ -224,11 +229,11 @@ def run_reference(args, world, rank):
         return 0
     budget = 150.0
     total = args.steps + args.warmup
-    probe = OracleBand(16)
+    probe = OracleBand(16, args.lattice)
     probe.step(1)
     per_node = probe.step(2) / (2 * probe.nodes)
     rows = int(max(4, min(512, budget / total / per_node / NX)))
-    band = OracleBand(rows)
+    band = OracleBand(rows, args.lattice)
     band.step(args.warmup)
     dt = band.step(args.steps)
     v = band.nodes * args.steps / dt / 1e6
@@ -236,7 +241,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+        "data": "synthetic", "config": {"workload": workload_name(NX, NY, args.lattice),
+                                        "nx": NX, "ny": NY, "lattice": f"D2Q{args.lattice}",
                                         "sample_rows": rows},
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"each step: one oracle step on a periodic {NX}x{rows} band "
@@ -334,6 +340,7 @@ def run_gpu(args, world, rank, local):
 
     nx, ny = (int(v) for v in args.size.lower().split("x"))
     w = W.large_multi_droplet(nx=nx, ny=ny, noise_amp=0.0)
+    w.lattice = args.lattice
     sim = pkg.Simulation.from_workload(w, storage=args.storage)
     lay = sim.layout()
     stream = torch.cuda.current_stream()
@@ -379,9 +386,9 @@ def run_gpu(args, world, rank, local):
 
     # ---- roofline of the fused kernel ----------------------------------------
     peak, peak_kind = measured_peaks()
-    b_node = 2 * 9 * BYTES[args.storage]
+    b_node = 2 * args.lattice * BYTES[args.storage]
     achieved = b_node * N * args.steps / t_local / 1e9
-    traffic = ncu_traffic(args.storage)
+    traffic = ncu_traffic(args.storage, args.lattice)
     clocks = clk.summary()
     sim.close()
     if rank != 0:
@@ -391,12 +398,11 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[args.storage], "data": "synthetic",
-        "config": {"workload": WORKLOAD if (nx, ny) == (NX, NY) else
-                   WORKLOAD.replace("8192x4096", f"{nx}x{ny}"), "nx": nx, "ny": ny,
-                   "lattice": "D2Q9",
+        "config": {"workload": workload_name(nx, ny, args.lattice), "nx": nx, "ny": ny,
+                   "lattice": f"D2Q{args.lattice}",
                    "storage": args.storage, "parallelism": f"replicas{world}",
                    "l2": "no flush: the 2 population buffers (2x%.2f GB) exceed L2" %
-                         (9 * BYTES[args.storage] * N / 1e9),
+                         (args.lattice * BYTES[args.storage] * N / 1e9),
                    "launch": {k: lay[k] for k in ("strip_width", "tile_rows", "grid_x",
                                                    "grid_y", "stages")}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -415,7 +421,7 @@ def run_gpu(args, world, rank, local):
     if not args.no_serving:
         line["serving"] = measure_serving(pkg, torch, W)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(lattice=args.lattice)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -432,6 +438,8 @@ def main(argv=None):
                     help="skip the batched parameter-sweep measurement")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving measurement")
+    ap.add_argument("--lattice", type=int, default=9, choices=[9, 21],
+                    help="velocity set: D2Q9 (the headline) or D2Q21 on the same drops and wall")
     ap.add_argument("--size", default=f"{NX}x{NY}",
                     help="lattice size NXxNY (the same recipe at another size, for profiling)")
     args = ap.parse_args(argv)
