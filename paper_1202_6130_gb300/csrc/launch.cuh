@@ -16,7 +16,8 @@ namespace lbm {
 // (Measured on GB300, 8192x4096: D2Q9 NS 4 / MINB 8 for FP32 and MINB 10 for
 // 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12; D2Q21 needs NS >= R + 2
 // = 5, and NS 5 with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3
-// by 21% and 5%.)
+// by 21% and 5%.  Shared memory holds 16-bit D2Q21 at 5 CTAs of 64 threads
+// (node pairs); a 6-CTA register target changed nothing.)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
   static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6)) : 5;

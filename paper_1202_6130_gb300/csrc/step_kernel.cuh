@@ -99,15 +99,15 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int CHUNKS = W / 32;  // wall-flag words per row
   static constexpr int FLAG_SLOT = ((CHUNKS * 4 + 127) / 128) * 128;
   static constexpr int STAGE = NBOX * BOXSLOT + FLAG_SLOT;
-  // Nodes per thread: D2Q9 with FP32 arithmetic updates two adjacent columns
-  // per thread with packed FP32 instructions; otherwise one.
-  // Nodes per thread: D2Q9 with FP32 arithmetic updates adjacent columns in
-  // packed FP32 pairs, one pair per thread; otherwise one node.  (The paired
-  // march takes any number of pairs per thread; two pairs, i.e. 32-thread
-  // CTAs for 16-bit storage, measured 25% slower than one on GB300.)
-  static constexpr int V = (Q == 9 && sizeof(T) == 4) ? 2 : 1;
+  // Nodes per thread: with FP32 arithmetic (D2Q9; D2Q21 with 16-bit
+  // storage) adjacent columns are updated in packed FP32 pairs, one pair per
+  // thread; otherwise one node.  (The paired march takes any number of pairs
+  // per thread; two pairs, i.e. 32-thread CTAs for 16-bit D2Q9, measured 25%
+  // slower than one on GB300.)
+  static constexpr int V = (sizeof(T) == 4 && (Q == 9 || sizeof(S) == 2)) ? 2 : 1;
   static constexpr int NT = W / V;                       // threads per CTA
-  static constexpr int RO = V >= 2 ? 2 : R;              // ring column of node 0 (even for pairs)
+  // Ring column of node 0: at least R, and even for pairs.
+  static constexpr int RO = V >= 2 ? (R + 1) / 2 * 2 : R;
   static constexpr int RING_W = W + 2 * RO;
   static constexpr int RING_H = 2 * R + 2;
   static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
@@ -467,30 +467,32 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
   return true;
 }
 
-// Two nodes per thread (D2Q9, FP32 arithmetic): thread t updates columns 2t
-// and 2t + 1 of the strip.  Same schedule and stage layout as march_segment;
-// the node arithmetic runs on packed FP32 pairs, aligned pairs of stored
+// Two nodes per thread (FP32 arithmetic): thread t updates columns 2t and
+// 2t + 1 of the strip.  Same schedule and stage layout as march_segment; the
+// node arithmetic runs on packed FP32 pairs, aligned pairs of stored
 // populations and of psi are moved with one 64- or 32-bit access, and each
-// population row is stored as pairs.  Wall terms, ghost images, the halo psi
-// and a pair that straddles the lattice's right edge fall back to per-node
-// code.
-template <typename S, int W, int NS, int MODE, typename Args>
+// population row is stored as pairs.  With R = 1 (D2Q9) the populations of a
+// row stay in registers from its psi pass to its collision; with R > 1
+// (D2Q21) the collision re-reads them from the row's stage, as march_segment
+// does.  Wall terms, ghost images, the halo psi and a pair that straddles the
+// lattice's right edge fall back to per-node code.
+template <int Q, typename S, int W, int NS, int MODE, typename Args>
 __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const CUtensorMap* flg,
                                                  const Args& a, int x0, int y0, int Lr, bool rev,
-                                                 const StepSmem<9, S, W, NS>& sm, uint32_t& g) {
-  constexpr int Q = 9;
+                                                 const StepSmem<Q, S, W, NS>& sm, uint32_t& g) {
   using Sh = StepShape<Q, S, W, NS>;
   using L = Lattice<Q>;
   using E = EqConst<Q>;
   using C = Codec<S>;
   using PR = Pair<S>;
   using T = float;
-  constexpr int R = 1;
+  constexpr int R = Sh::R;
   constexpr int GX = Sh::GX;
   constexpr int GY = Sh::GY;
   constexpr int RO = Sh::RO;
   constexpr int P = Sh::V / 2;  // node pairs per thread
-  static_assert(Sh::V % 2 == 0 && Sh::kRegs, "paired march");
+  constexpr bool kRegs = Sh::kRegs;
+  static_assert(Sh::V % 2 == 0 && RO % 2 == 0 && RO >= R, "paired march");
   unsigned char* const stages = sm.stages;
   uint64_t* const bars = sm.bars;
   T* const ring = sm.ring;
@@ -558,27 +560,43 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     return pseudo_potential<Q, T>(a.phys, rho);
   };
 
-  F2 fnext[P][Q];
-  F2 rho_next[P];  // rho of those populations, summed once in table order
+  // The thread's columns lie in one 32-column flag chunk.
+  auto flags_of = [&](const unsigned char* stage) -> uint32_t {
+    return wall_on ? reinterpret_cast<const uint32_t*>(stage + Sh::NBOX * Sh::BOXSLOT)[xa >> 5]
+                   : 0u;
+  };
+
+  // kRegs: populations and rho (summed once, in table order) of the row whose
+  // psi was just formed, collided in the next iteration.
+  F2 fnext[kRegs ? P : 1][kRegs ? Q : 1];
+  F2 rho_next[P];
   uint32_t flag_next = 0;
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
   int k = 0;
-#pragma unroll 2
+  // With kRegs, unrolled by two so that the carried registers alternate
+  // between two sets instead of being copied.
+  constexpr int kUnroll = kRegs ? 2 : 1;
+#pragma unroll kUnroll
   for (; k < K; ++k) {
     if (!mbar_wait_bounded(&bars[s], phase, a.wait_ns)) *s_abort = 1;
     const unsigned char* stb = stages + s * Sh::STAGE;
     const S* st = reinterpret_cast<const S*>(stb);
 
+    // Populations, rho and wall flags of the row collided in this iteration
+    // (row k - R).
     F2 f[P][Q];
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[p][i] = fnext[p][i];
     F2 rho_cur[P];
+    uint32_t flag = 0;
+    if constexpr (kRegs) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) rho_cur[p] = rho_next[p];
-    const uint32_t flag = flag_next;
+      for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[p][i] = fnext[p][i];
+        rho_cur[p] = rho_next[p];
+      }
+      flag = flag_next;
+    }
 
     // psi of node row k for the thread's columns, then the halo columns.
     T* ring_row = ring + (k % Sh::RING_H) * Sh::RING_W;
@@ -588,17 +606,15 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
       static_for<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const F2 v = load_pair(st, ic, p);
-        fnext[p][i] = v;
+        if constexpr (kRegs) fnext[p][i] = v;
         rho = (i == 0) ? v : rho + v;
       });
       const T pa = pseudo_potential<Q, T>(a.phys, rho.x());
       const T pb = pseudo_potential<Q, T>(a.phys, rho.y());
       *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = make_float2(pa, pb);
-      rho_next[p] = rho;
+      if constexpr (kRegs) rho_next[p] = rho;
     }
-    // the thread's columns lie in one 32-column flag chunk
-    flag_next = wall_on ? reinterpret_cast<const uint32_t*>(stb + Sh::NBOX * Sh::BOXSLOT)[xa >> 5]
-                        : 0u;
+    if constexpr (kRegs) flag_next = flags_of(stb);
     if (tid < 2 * R) {
       const int xl = tid < R ? tid - R : W + tid - R;
       ring_row[xl + RO] = psi_at(st, xl);
@@ -606,8 +622,9 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     __syncthreads();
     if (*s_abort) break;
 
+    // Every thread has finished iteration k - 1: recycle the stage it last used.
     if (tid == kIss) {
-      const int fr = k - 1;
+      const int fr = k - 1 - (kRegs ? 0 : R);
       if (fr >= 0 && fr + NS < K) {
         issue(fr + NS);
         issued = fr + NS + 1;
@@ -617,43 +634,91 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     if (k >= 2 * R) {
       const int ko = k - R;
       const int yo = ybase + ds * ko;
+      if constexpr (!kRegs) {
+        const int so = s >= R ? s - R : s - R + NS;  // stage of row k - R
+        const unsigned char* sto = stages + so * Sh::STAGE;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          static_for<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            f[p][i] = load_pair(reinterpret_cast<const S*>(sto), ic, p);
+            rho_cur[p] = (i == 0) ? f[p][i] : rho_cur[p] + f[p][i];
+          });
+        }
+        flag = flags_of(sto);
+      }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const int xp = x + 2 * p;           // first column of pair p
         const bool pair_ok = xp + 1 < a.nx;  // both nodes exist
         F2 (&f_)[Q] = f[p];
-        // rho of both nodes carried from the psi pass (table order); j with
+        // rho of both nodes in table order (the psi pass's sum); j (D2Q9:
         // the diagonal differences f5 - f7 and f8 - f6 shared by its two
-        // components.
+        // components; otherwise in table order).
         const F2 rho = rho_cur[p];
-        const F2 d57 = f_[5] - f_[7], d86 = f_[8] - f_[6];
-        const F2 jx = ((f_[1] - f_[3]) + d57) + d86;
-        const F2 jy = ((f_[2] - f_[4]) + d57) - d86;
+        F2 jx, jy;
+        if constexpr (Q == 9) {
+          const F2 d57 = f_[5] - f_[7], d86 = f_[8] - f_[6];
+          jx = ((f_[1] - f_[3]) + d57) + d86;
+          jy = ((f_[2] - f_[4]) + d57) - d86;
+        } else {
+          jx = F2::splat(0.f);
+          jy = F2::splat(0.f);
+          static_for<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            if constexpr (L::cx(i) != 0) jx = fma2(f_[i], F2::splat(T(L::cx(i))), jx);
+            if constexpr (L::cy(i) != 0) jy = fma2(f_[i], F2::splat(T(L::cy(i))), jy);
+          });
+        }
         const F2 inv_rho(t_rcp<float>(rho.x()), t_rcp<float>(rho.y()));
         const F2 ux = jx * inv_rho;
         const F2 uy = jy * inv_rho;
 
-        // Neighbour psi: three aligned pairs per ring row cover the pair's
-        // columns and one more on either side.
+        // Neighbour psi, sum_i w_i psi(x + c_i) c_i.
         F2 sfx = F2::splat(0.f), sfy = F2::splat(0.f), psi_c;
-        static_for<0, 3>([&](auto rc) {
-          constexpr int cy = decltype(rc)::value - 1;
-          const T* row = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa + 2 * p;
-          const float2 A = *reinterpret_cast<const float2*>(row - 2);
-          const float2 B = *reinterpret_cast<const float2*>(row);
-          const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
-          const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
-          if constexpr (cy == 0) {
-            psi_c = p0;
-            sfx = fma2(pp - pm, F2::splat(T(L::w(1))), sfx);  // (1,0) and (-1,0)
-          } else {
-            // (0,cy): weight w_axis; (+-1, cy): weight w_diag
-            constexpr T sg = cy > 0 ? T(1) : T(-1);
-            sfy = fma2(p0, F2::splat(sg * T(L::w(2))), sfy);
-            sfy = fma2(pp + pm, F2::splat(sg * T(L::w(5))), sfy);
-            sfx = fma2(pp - pm, F2::splat(T(L::w(5))), sfx);
-          }
-        });
+        if constexpr (Q != 9) {
+          // Ring row of node row yo + c_y; the psi pair at column offset c_x
+          // is one aligned pair (c_x even) or the halves of two.
+          auto ring_at = [&](int cy, int o) -> float2 {
+            return *reinterpret_cast<const float2*>(
+                ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa + 2 * p + o);
+          };
+          psi_c = F2(ring_at(0, 0));
+          static_for<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int cx = L::cx(i), cy = L::cy(i);
+            if constexpr (i == L::REST) return;
+            F2 nb;
+            if constexpr ((cx & 1) == 0) {
+              nb = F2(ring_at(cy, cx));
+            } else {
+              nb = F2(ring_at(cy, cx - 1).y, ring_at(cy, cx + 1).x);
+            }
+            if constexpr (cx != 0) sfx = fma2(nb, F2::splat(T(L::w(i) * cx)), sfx);
+            if constexpr (cy != 0) sfy = fma2(nb, F2::splat(T(L::w(i) * cy)), sfy);
+          });
+        } else {
+          // D2Q9: three aligned pairs per ring row cover the pair's columns
+          // and one more on either side.
+          static_for<0, 3>([&](auto rc) {
+            constexpr int cy = decltype(rc)::value - 1;
+            const T* row = ring + ((ko + ds * cy) & (Sh::RING_H - 1)) * Sh::RING_W + RO + xa + 2 * p;
+            const float2 A = *reinterpret_cast<const float2*>(row - 2);
+            const float2 B = *reinterpret_cast<const float2*>(row);
+            const float2 Cc = *reinterpret_cast<const float2*>(row + 2);
+            const F2 pm(A.y, B.x), p0(B), pp(B.y, Cc.x);   // psi at c_x = -1, 0, +1
+            if constexpr (cy == 0) {
+              psi_c = p0;
+              sfx = fma2(pp - pm, F2::splat(T(L::w(1))), sfx);  // (1,0) and (-1,0)
+            } else {
+              // (0,cy): weight w_axis; (+-1, cy): weight w_diag
+              constexpr T sg = cy > 0 ? T(1) : T(-1);
+              sfy = fma2(p0, F2::splat(sg * T(L::w(2))), sfy);
+              sfy = fma2(pp + pm, F2::splat(sg * T(L::w(5))), sfy);
+              sfx = fma2(pp - pm, F2::splat(T(L::w(5))), sfx);
+            }
+          });
+        }
 
         // Force: F_FF, then the wall terms on flagged chunks, then body force.
         const F2 mg = F2::splat(-a.phys.G) * psi_c;
@@ -731,15 +796,12 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
               }
             });
             {  // mass closure of the rest population (FP32 arithmetic)
-              F2 moving = f_[1];
-              moving += f_[2];
-              moving += f_[3];
-              moving += f_[4];
-              moving += f_[5];
-              moving += f_[6];
-              moving += f_[7];
-              moving += f_[8];
-              f_[0] = rho - moving;
+              constexpr int i0 = L::REST == 0 ? 1 : 0;
+              F2 moving = f_[i0];
+#pragma unroll
+              for (int i = i0 + 1; i < Q; ++i)
+                if (i != L::REST) moving += f_[i];
+              f_[L::REST] = rho - moving;
             }
             // Encode both nodes once (stochastic rounding: bits from the node pair
             // and the step), then the primary store plus periodic images.
@@ -846,7 +908,7 @@ __device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensor
                                           const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                           uint64_t policy) {
   if constexpr (StepShape<Q, S, W, NS>::V >= 2)
-    return march_segment_v2<S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g);
+    return march_segment_v2<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g);
   else
     return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g, policy);
 }

@@ -188,15 +188,21 @@ def test_fp64_ragged_and_multi_tile_match_oracle(pkg, case):
 
 PAIRED_CASES = [dict(nx=67, ny=35, tile_rows=5), dict(nx=1, ny=16, tile_rows=4),
                 dict(nx=3, ny=1, tile_rows=0), dict(nx=129, ny=7, tile_rows=3, uwall=True,
-                                                    body=(1e-5, 0.0))]
+                                                    body=(1e-5, 0.0)),
+                # D2Q21 (R = 3): odd widths, several tiles, a moving wall, the Eq. EOS fluid
+                dict(nx=67, ny=35, lattice=21, tile_rows=5), dict(nx=3, ny=9, lattice=21, tile_rows=2),
+                dict(nx=131, ny=13, lattice=21, tile_rows=4, uwall=True, body=(1e-5, 0.0)),
+                dict(nx=61, ny=47, lattice=21, tile_rows=6, eos=True)]
 
 
-@pytest.mark.parametrize("case", PAIRED_CASES, ids=lambda c: "x".join(map(str, (c["nx"], c["ny"]))))
+@pytest.mark.parametrize("case", PAIRED_CASES, ids=lambda c: "x".join(map(str, (c["nx"], c["ny"])))
+                         + f"_q{c.get('lattice', 9)}")
 @pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16s", 2e-2)])
 def test_paired_path_ragged_sizes_match_oracle(pkg, case, storage, tol):
-    """The two-nodes-per-thread path on odd widths (a lone last column), a
-    one-column and a one-row lattice, many tiles: FP32 within 1e-5 of the
-    oracle after 40 steps, 16-bit storage within its rounding."""
+    """The two-nodes-per-thread path (D2Q9 in FP32 and 16-bit storage, D2Q21 in
+    16-bit storage; D2Q21 FP32 runs one node per thread) on odd widths (a lone
+    last column), a one-column and a one-row lattice, many tiles: FP32 within
+    1e-5 of the oracle after 40 steps, 16-bit storage within its rounding."""
     case = dict(case)
     tr = case.pop("tile_rows")
     w = _small_case(**case)
