@@ -27,7 +27,7 @@ struct lbm_ctx {
   int64_t pitch = 0, rows = 0, plane = 0;
   void* buf[2] = {nullptr, nullptr};
   int cur = 0;  // buffer holding the current state
-  CUtensorMap tmap[2];
+  PopMaps tmap[2];       // population maps of buffer 0 and 1 (one per box depth)
   // wall (compute precision: double for FP64 storage, float otherwise)
   void* wall_phie = nullptr;
   void* wall_sx = nullptr;
@@ -178,12 +178,16 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
   cuuint64_t dims[3] = {(cuuint64_t)(c->p.nx + 2 * Sh::GX), (cuuint64_t)c->rows, (cuuint64_t)Q};
   cuuint64_t strides[2] = {(cuuint64_t)(c->pitch * sizeof(S)),
                            (cuuint64_t)(c->plane * sizeof(S))};
-  cuuint32_t box[3] = {(cuuint32_t)Sh::BW, 1, (cuuint32_t)Sh::BD};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&c->tmap[which], tma_type<S>(), 3, c->buf[which], dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  c->tmap[which] = PopMaps{};
+  for (int k = 0; k < Sh::NMAP; ++k) {
+    // One box: a row of BW elements of Sh::kTab.depth[k] consecutive planes.
+    cuuint32_t box[3] = {(cuuint32_t)Sh::BW, 1, (cuuint32_t)Sh::kTab.depth[k]};
+    CUresult r = enc(&c->tmap[which].m[k], tma_type<S>(), 3, c->buf[which], dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  }
   return LBM_OK;
 }
 
@@ -309,7 +313,7 @@ int run_pass(lbm_ctx* c, int mode, double* o_rho, double* o_ux, double* o_uy, in
              S* fout) {
   const auto a = make_args<Q, S>(c, c->cur, fout, o_rho, o_ux, o_uy, momentum);
   // Without walls the flag map is never read; the population map stands in.
-  const CUtensorMap& fm = c->has_wall ? c->flag_map : c->tmap[c->cur];
+  const CUtensorMap& fm = c->has_wall ? c->flag_map : c->tmap[c->cur].m[0];
   CK(c, launch_step<Q, S>(c->tmap[c->cur], fm, a, dim3(c->grid_x, c->grid_y), c->stream, mode));
   return LBM_OK;
 }
@@ -916,7 +920,7 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     std::memset(&m, 0, sizeof m);
     m.map[0] = c->tmap[0];
     m.map[1] = c->tmap[1];
-    m.flags = c->has_wall ? c->flag_map : c->tmap[0];
+    m.flags = c->has_wall ? c->flag_map : c->tmap[0].m[0];
     b->versions[i] = c->version;
     b->cur0[i] = c->cur;
   }

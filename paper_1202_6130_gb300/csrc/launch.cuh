@@ -16,13 +16,13 @@ namespace lbm {
 // (Measured on GB300, 8192x4096: D2Q9 NS 4 / MINB 8 for FP32 and MINB 10 for
 // 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12; D2Q21 needs NS >= R + 2
 // = 5, and NS 5 with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3
-// by 21% and 5%.  Shared memory holds 16-bit D2Q21 at 5 CTAs of 64 threads
-// (node pairs); a 6-CTA register target changed nothing.)
+// by 21% and 5%.  16-bit D2Q21 runs 6 CTAs of 64 threads (node pairs) once
+// its plane groups arrive as boxes of depth 1, 3 and 7 (37 KB per CTA).)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
   static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6)) : 5;
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
-                                       : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 5));
+                                       : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 6));
   // The batch kernel carries its tile loop on top of the march: 16-bit D2Q9
   // targets 8 CTAs per SM there, so that it does not spill.
   static constexpr int BATCH_MINB = (Q == 9 && sizeof(S) == 2) ? 8 : MINB;
@@ -33,7 +33,7 @@ using ConfigShape = StepShape<Q, S, StepConfig<Q, S>::W, StepConfig<Q, S>::NS>;
 
 // Launches the fused step (mode kModeStep) or the read-out pass (kModeMoments).
 template <int Q, typename S>
-cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
+cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
                         const StepArgs<typename Codec<S>::T, S>& a, dim3 grid,
                         cudaStream_t stream, int mode);
 

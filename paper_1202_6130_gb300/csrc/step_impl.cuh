@@ -17,7 +17,7 @@ static cudaError_t prepare_kernel() {
 }
 
 template <int Q, typename S>
-cudaError_t launch_step(const CUtensorMap& src, const CUtensorMap& flags,
+cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
                         const StepArgs<typename Codec<S>::T, S>& a, dim3 grid,
                         cudaStream_t stream, int mode) {
   using Cfg = StepConfig<Q, S>;
@@ -108,7 +108,7 @@ template <int Q, typename S> int batch_ctas_per_sm() {
 }  // namespace lbm
 
 #define LBM_INSTANTIATE_STEP(Q, S)                                                         \
-  template cudaError_t lbm::launch_step<Q, S>(const CUtensorMap&, const CUtensorMap&,      \
+  template cudaError_t lbm::launch_step<Q, S>(const PopMaps&, const CUtensorMap&,      \
                                               const lbm::StepArgs<lbm::Codec<S>::T, S>&,   \
                                               dim3, cudaStream_t, int);                    \
   template int lbm::step_ctas_per_sm<Q, S>();                                            \

@@ -82,6 +82,13 @@ template <int MODE, typename Args> __device__ __forceinline__ void advance_key(c
   if constexpr (MODE == kModeStep) a.rng[a.rng_idx ^ 1] = a.rng[a.rng_idx] + 1u;
 }
 
+// TMA maps of one population buffer, one per distinct box depth of the
+// lattice's plane groups (D2Q9 uses one, D2Q21 three).
+constexpr int kMaxMaps = 3;
+struct PopMaps {
+  CUtensorMap m[kMaxMaps];
+};
+
 template <int Q, typename S, int W, int NS> struct StepShape {
   using L = Lattice<Q>;
   using P = Planes<Q>;
@@ -90,15 +97,14 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int GX = ghost_x<S, R>();
   static constexpr int GY = ghost_y<R>();
   static constexpr int BW = W + 2 * GX;  // box width (elements)
-  // Planes are grouped by c_y; every group size of D2Q9 is 3 (one box of depth
-  // 3 per group), D2Q21 groups have 7, 3 and 1 planes (boxes of depth 1).
-  static constexpr int BD = (Q == 9) ? 3 : 1;
-  static constexpr int NBOX = Q / BD;
-  static constexpr int BOXSLOT = ((BD * BW * (int)sizeof(S) + 127) / 128) * 128;  // bytes
-  static constexpr int BOXSLOT_E = BOXSLOT / (int)sizeof(S);
+  // Planes are grouped by c_y (one group per c_y = -R..R, consecutive planes);
+  // each group arrives as one TMA box as deep as the group: D2Q9 groups have
+  // 3 planes, D2Q21 groups 1, 3, 3, 7, 3, 3 and 1.  A tensor map fixes its
+  // box, so there is one map per distinct depth.  Every box lands in a
+  // 128-byte aligned slot of the stage.
+  static constexpr int NBOX = 2 * R + 1;
   static constexpr int CHUNKS = W / 32;  // wall-flag words per row
   static constexpr int FLAG_SLOT = ((CHUNKS * 4 + 127) / 128) * 128;
-  static constexpr int STAGE = NBOX * BOXSLOT + FLAG_SLOT;
   // Nodes per thread: with FP32 arithmetic (D2Q9; D2Q21 with 16-bit
   // storage) adjacent columns are updated in packed FP32 pairs, one pair per
   // thread; otherwise one node.  (The paired march takes any number of pairs
@@ -110,33 +116,63 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int RO = V >= 2 ? (R + 1) / 2 * 2 : R;
   static constexpr int RING_W = W + 2 * RO;
   static constexpr int RING_H = 2 * R + 2;
-  static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
-                              RING_H * RING_W * (int)sizeof(T) + 16;
   static constexpr uint32_t TX_POP = Q * BW * (uint32_t)sizeof(S);
   static constexpr uint32_t TX_FLAGS = CHUNKS * 4;
   // Populations of the node row being collided stay in registers (R = 1) or
   // are re-read from its stage (R > 1, where R rows of Q values would not fit).
   static constexpr bool kRegs = (R == 1);
-  // Element offset of population i's pulled row inside a stage, and the c_y
-  // shared by the planes of box j: compile-time tables.
+  // Compile-time stage layout: per group j its c_y, first plane, depth, byte
+  // offset in the stage and tensor map (by depth); per population i the
+  // element offset of its pulled row inside a stage.
   struct Tables {
     int pop_row[Q];
     int box_cy[NBOX];
+    int box_plane[NBOX];
+    int box_depth[NBOX];
+    int box_off[NBOX];
+    int box_map[NBOX];
+    int depth[kMaxMaps];
+    int nmap;
+    int pop_bytes;
   };
   static constexpr Tables make_tables() {
     Tables t{};
+    int off = 0;
+    for (int j = 0; j < NBOX; ++j) {
+      const int cy = j - R;
+      int first = Q, n = 0;
+      for (int i = 0; i < Q; ++i) {
+        if (L::cy(i) != cy) continue;
+        ++n;
+        if (P::kTable.plane[i] < first) first = P::kTable.plane[i];
+      }
+      t.box_cy[j] = cy;
+      t.box_plane[j] = first;
+      t.box_depth[j] = n;
+      t.box_off[j] = off;
+      int k = 0;
+      while (k < t.nmap && t.depth[k] != n) ++k;
+      if (k == t.nmap) t.depth[t.nmap++] = n;
+      t.box_map[j] = k;
+      off += (n * BW * (int)sizeof(S) + 127) / 128 * 128;
+    }
+    t.pop_bytes = off;
     for (int i = 0; i < Q; ++i) {
-      const int p = P::kTable.plane[i];
-      t.pop_row[i] = (p / BD) * BOXSLOT_E + (p % BD) * BW;
-      if (p % BD == 0) t.box_cy[p / BD] = L::cy(i);
+      const int j = L::cy(i) + R;
+      t.pop_row[i] = t.box_off[j] / (int)sizeof(S) + (P::kTable.plane[i] - t.box_plane[j]) * BW;
     }
     return t;
   }
   static constexpr Tables kTab = make_tables();
+  static constexpr int NMAP = kTab.nmap;
+  static constexpr int POP_BYTES = kTab.pop_bytes;  // flags slot follows the boxes
+  static constexpr int STAGE = POP_BYTES + FLAG_SLOT;
+  static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
+                              RING_H * RING_W * (int)sizeof(T) + 16;
   static_assert(W % 32 == 0 && W >= 64 && CHUNKS <= 256, "strip width");
   static_assert(NT % 32 == 0 && NT >= 32, "threads per CTA");
   static_assert(NS >= R + 2, "pipeline depth");
-  static_assert(Q % BD == 0, "box depth");
+  static_assert(NMAP <= kMaxMaps && BW <= 256, "tensor-map boxes");
 };
 
 // Shared-memory carve-up of one CTA: NS stages, their mbarriers, the psi ring
@@ -188,7 +224,7 @@ __device__ __forceinline__ uint64_t step_smem_init(const StepSmem<Q, S, W, NS>& 
 // arithmetic is the same in either direction.  Returns false if a stage never
 // arrived (the status word then has kStatusTimeout).
 template <int Q, typename S, int W, int NS, int MODE, typename Args>
-__device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUtensorMap* flg,
+__device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensorMap* flg,
                                               const Args& a, int x0, int y0, int Lr, bool rev,
                                               const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                               uint64_t policy) {
@@ -235,13 +271,15 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
       constexpr int cy = Sh::kTab.box_cy[j];
       // Normal L2 priority: the 2R halo rows of a segment are read again by
       // the segment below a few microseconds later and should hit in L2.
-      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD);
+      constexpr int off = Sh::kTab.box_off[j], map = Sh::kTab.box_map[j];
+      constexpr int plane = Sh::kTab.box_plane[j];
+      tma_load_3d(st + off, &src->m[map], &bars[s], x0, ynode - cy + GY, plane);
     });
-    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, flg, &bars[s], x0 >> 5, ynode);
+    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], x0 >> 5, ynode);
   };
   int issued = 0;
   if (tid == kIss) {
-    prefetch_tensormap(src);
+    static_for<0, Sh::NMAP>([&](auto kc) { prefetch_tensormap(&src->m[decltype(kc)::value]); });
     if (wall_on) prefetch_tensormap(flg);
     const int n0 = min(NS, K);
 #pragma unroll 1
@@ -265,7 +303,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
     return pseudo_potential<Q, T>(a.phys, rho);
   };
   auto flags_of = [&](const unsigned char* st) -> uint32_t {
-    return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::NBOX * Sh::BOXSLOT)[warp] : 0u;
+    return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::POP_BYTES)[warp] : 0u;
   };
 
   T fnext[Q];            // kRegs: populations of the row whose psi was just formed
@@ -477,7 +515,7 @@ __device__ __forceinline__ bool march_segment(const CUtensorMap* src, const CUte
 // does.  Wall terms, ghost images, the halo psi and a pair that straddles the
 // lattice's right edge fall back to per-node code.
 template <int Q, typename S, int W, int NS, int MODE, typename Args>
-__device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const CUtensorMap* flg,
+__device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUtensorMap* flg,
                                                  const Args& a, int x0, int y0, int Lr, bool rev,
                                                  const StepSmem<Q, S, W, NS>& sm, uint32_t& g) {
   using Sh = StepShape<Q, S, W, NS>;
@@ -522,13 +560,15 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
     static_for<0, Sh::NBOX>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
       constexpr int cy = Sh::kTab.box_cy[j];
-      tma_load_3d(st + j * Sh::BOXSLOT, src, &bars[s], x0, ynode - cy + GY, j * Sh::BD);
+      constexpr int off = Sh::kTab.box_off[j], map = Sh::kTab.box_map[j];
+      constexpr int plane = Sh::kTab.box_plane[j];
+      tma_load_3d(st + off, &src->m[map], &bars[s], x0, ynode - cy + GY, plane);
     });
-    if (wall_on) tma_load_2d(st + Sh::NBOX * Sh::BOXSLOT, flg, &bars[s], x0 >> 5, ynode);
+    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], x0 >> 5, ynode);
   };
   int issued = 0;
   if (tid == kIss) {
-    prefetch_tensormap(src);
+    static_for<0, Sh::NMAP>([&](auto kc) { prefetch_tensormap(&src->m[decltype(kc)::value]); });
     if (wall_on) prefetch_tensormap(flg);
     const int n0 = min(NS, K);
 #pragma unroll 1
@@ -562,7 +602,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
 
   // The thread's columns lie in one 32-column flag chunk.
   auto flags_of = [&](const unsigned char* stage) -> uint32_t {
-    return wall_on ? reinterpret_cast<const uint32_t*>(stage + Sh::NBOX * Sh::BOXSLOT)[xa >> 5]
+    return wall_on ? reinterpret_cast<const uint32_t*>(stage + Sh::POP_BYTES)[xa >> 5]
                    : 0u;
   };
 
@@ -903,7 +943,7 @@ __device__ __forceinline__ bool march_segment_v2(const CUtensorMap* src, const C
 // Marches one segment with the variant the shape selects (one or two nodes
 // per thread).
 template <int Q, typename S, int W, int NS, int MODE, typename Args>
-__device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensorMap* flg,
+__device__ __forceinline__ bool march_any(const PopMaps* src, const CUtensorMap* flg,
                                           const Args& a, int x0, int y0, int Lr, bool rev,
                                           const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                           uint64_t policy) {
@@ -920,7 +960,7 @@ __device__ __forceinline__ bool march_any(const CUtensorMap* src, const CUtensor
 // such a row is an L2 hit instead of a DRAM read.
 template <int Q, typename S, int W, int NS, int MODE, int MINB>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
-    step_kernel(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap flg,
+    step_kernel(const __grid_constant__ PopMaps src, const __grid_constant__ CUtensorMap flg,
                 const StepArgs<typename Codec<S>::T, S> a) {
   extern __shared__ unsigned char smem_raw[];
   const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
@@ -943,7 +983,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
 // A lattice of a batch: TMA maps of its two population buffers and of its wall
 // flags (in device memory; map[d] reads buffer d).
 template <typename T, typename S> struct BatchMember {
-  CUtensorMap map[2];
+  PopMaps map[2];
   CUtensorMap flags;
 };
 
