@@ -330,7 +330,8 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
     64x32 .. 1024x512 (seed 2), each with its own tau, G, G_R, G_A and a drop or
     a sheared film.  Times `steps` steps run one lattice after another (one
     launch per lattice per step) against the same steps of all lattices in one
-    batch (one fused launch per step, two-step CUDA graph, autotuned tiles)."""
+    batch (one fused launch per 32-lattice chunk per step, chunks on forked
+    streams, two-step CUDA graph, autotuned tiles)."""
     ws = W.batch_sweep(n=n, seed=2)
     nodes = sum(w.nx * w.ny for w in ws)
     sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
@@ -346,6 +347,7 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
     for sm in sims:
         b.add(sm)
     tune = b.autotune(steps_per_trial=10)
+    launches = b.launches_per_step()
     b.step(4)
     b.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -365,7 +367,7 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
             "batched_mlups": nodes * steps / t_bat / 1e6,
             "batched_device_mlups": nodes * steps / t_bat_dev / 1e6,
             "speedup": t_seq / t_bat, "tiling": tune, "finite": finite,
-            "gpu_launches_batched": steps}
+            "gpu_launches_batched": steps * launches}
 
 
 def run_gpu(args, world, rank, local):

@@ -219,12 +219,13 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
                        double core_lambda, double core_cut, double tail_exp, double tail_cut,
                        double phi_cut, double* phi_s, double* psi_r, double* psi_a);
 
-/* ---- batches: many lattices advanced by one launch per step ---------------- */
+/* ---- batches: many lattices advanced by shared launches --------------------- */
 
-/* A batch advances several contexts (its members) together: every time step of
- * every member is one launch of one fused kernel, whose CTAs march a list of
- * (member, strip, segment) tiles; two consecutive steps are captured once in a
- * CUDA graph and replayed.  Members must share lattice and storage but may
+/* A batch advances several contexts (its members) together: every time step is
+ * one launch of one fused kernel per chunk of up to 32 members, whose CTAs march
+ * a list of (member, strip, segment) tiles; the chunks run on streams forked
+ * from the batch stream, and two consecutive steps are captured once in a CUDA
+ * graph and replayed.  Members must share lattice and storage but may
  * differ in size and in every physical parameter.  Members stay owned by the
  * caller (destroy a member only after removing it), keep their own device
  * memory, and can still be read with lbm_moments and friends between batch
@@ -242,6 +243,9 @@ int lbm_batch_create(const lbm_allocator* a, void* cuda_stream, lbm_batch** out)
 int lbm_batch_add(lbm_batch* b, lbm_ctx* c);
 int lbm_batch_remove(lbm_batch* b, lbm_ctx* c);
 int lbm_batch_size(const lbm_batch* b, int32_t* n);
+/* Kernel launches per batch time step: the number of member chunks (members
+ * divided by 32, rounded up; 0 for an empty batch). */
+int lbm_batch_launches_per_step(const lbm_batch* b, int32_t* n);
 /* Tile shape: tile_rows rows per segment (0: each member's own choice) and
  * ctas persistent CTAs that deal the tiles round-robin (0: one CTA per tile). */
 int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas);

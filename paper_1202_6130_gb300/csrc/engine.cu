@@ -1097,6 +1097,12 @@ int lbm_batch_size(const lbm_batch* b, int32_t* n) {
   return LBM_OK;
 }
 
+int lbm_batch_launches_per_step(const lbm_batch* b, int32_t* n) {
+  if (!b || !n) return bfail(nullptr, LBM_EINVAL, "null argument");
+  *n = (int32_t)((b->members.size() + kBatchChunk - 1) / kBatchChunk);
+  return LBM_OK;
+}
+
 int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas) {
   int rc = batch_guard(b);
   if (rc) return rc;

@@ -187,8 +187,9 @@ class Simulation:
 
 
 class Batch:
-    """Several Simulations of one (lattice, storage) kind advanced together, one
-    fused launch per time step (lbm_batch_* of include/lbm.h)."""
+    """Several Simulations of one (lattice, storage) kind advanced together: one
+    fused launch per chunk of up to 32 members per time step (lbm_batch_* of
+    include/lbm.h)."""
 
     def __init__(self, stream=None, use_torch_allocator: bool = True, device=None):
         """``stream``: the stream batch steps run on; by default a new stream, so
@@ -220,6 +221,12 @@ class Batch:
 
     def synchronize(self):
         self.stream.synchronize()
+
+    def launches_per_step(self) -> int:
+        """Kernel launches per batch time step (one per chunk of up to 32 members)."""
+        n = ctypes.c_int32()
+        self._chk(self.lib.lbm_batch_launches_per_step(self.h, ctypes.byref(n)))
+        return n.value
 
     def set_tiling(self, tile_rows: int = 0, ctas: int = 0):
         self._chk(self.lib.lbm_batch_set_tiling(self.h, int(tile_rows), int(ctas)))

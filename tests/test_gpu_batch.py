@@ -158,6 +158,7 @@ def test_many_members_span_several_launch_chunks(pkg, storage):
     b = pkg.Batch()
     for s in sims:
         b.add(s)
+    assert b.launches_per_step() == 3
     b.step(2)
     b.step(3)
     for s, f in zip(sims, want):
