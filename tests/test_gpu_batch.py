@@ -100,8 +100,10 @@ def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s", "bf16s"])
 def test_d2q21_paper_fluid_batch_equals_members_alone_bitwise(pkg, storage):
-    """D2Q21 (one node per thread) with the Eq. EOS pseudo-potential and the
-    projection step; one member also has a body force."""
+    """D2Q21 (one node per thread in FP64 and FP32, node pairs in 16-bit
+    storage; plane groups as boxes of depth 1, 3 and 7) with the Eq. EOS
+    pseudo-potential and the projection step; one member also has a body
+    force."""
     th = 2.0 / 3.0
     kw = dict(eos=(0.25 * th, -0.25 * th, th, 0.222, 0.869), project=True)
     ws = []
