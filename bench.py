@@ -472,7 +472,7 @@ def run_gpu(args, world, rank, local):
         line["batch"] = measure_batch(pkg, torch, W)
     if not args.no_serving:
         line["serving"] = measure_serving(pkg, torch, W)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the host-core baseline is an N = 1 figure
         line["cpu_baseline"] = cpu_baseline(lattice=args.lattice)
     print(json.dumps(line), flush=True)
     return 0
