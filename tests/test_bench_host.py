@@ -52,3 +52,10 @@ def test_workload_names_and_fp64_constants():
     assert bench.FP64_FLOPS_PER_NODE[21] > bench.FP64_FLOPS_PER_NODE[9] > 0
     peak = 152 * bench.FP64_DFMA_PER_SM_CLK * 2 * 2.07e9 / 1e12
     assert peak == pytest.approx(1.25, rel=0.02)
+
+
+def test_all_cores_baseline_runs_the_oracle_in_spawned_processes():
+    r = bench.cpu_baseline_all_cores(lattice=9, rows=4, seconds=0.2)
+    assert r["kind"] == "oracle" and r["unit"] == "MLUPS"
+    assert r["cores"] == max(1, min(64, os.cpu_count() or 1))
+    assert r["value"] > 0 and str(r["cores"]) in r["sample"]
