@@ -6,6 +6,8 @@ and 1e-5 absolute in u (lattice units).  Wherever the oracle can run the same
 inputs, the comparison is element by element.  At the 8192x4096 size the
 oracle recomputes sampled nodes one by one from a periodic window around each.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -344,6 +346,56 @@ def test_full_size_fp32_sampled_nodes_match_oracle(pkg):
         fg = f1[:, y, x]
         err = np.max(np.abs(fg - fo) / np.maximum(np.abs(fo), 1e-3))
         assert err < 1e-5, (y, x, err)
+
+
+def _shift12(x):
+    """w_i shift_rho rounded to 12 significant bits (the storage shift lbm.h defines)."""
+    m, e = math.frexp(x)
+    return math.ldexp(round(math.ldexp(x, 12 - e)), e - 12)
+
+
+def _ulp16(v, storage):
+    """Unit in the last place of the 16-bit number holding v: binary16 (FP16S
+    stores the deviation scaled by 2^8, normal from 2^-14, subnormal step 2^-24)
+    or bfloat16 (8 significant bits)."""
+    a = np.abs(v)
+    if storage == "fp16s":
+        return 2.0 ** (np.floor(np.log2(np.maximum(a, 2.0 ** -14))) - 10)
+    return 2.0 ** (np.floor(np.log2(np.maximum(a, 2.0 ** -126))) - 7)
+
+
+@pytest.mark.parametrize("storage", ["fp16s", "bf16s"])
+def test_full_size_16bit_sampled_nodes_match_oracle(pkg, storage):
+    """One step of the 8192x4096 multi-droplet lattice in 16-bit storage, in
+    the launch shape the benchmark uses, after 20 warm-up steps; sampled nodes
+    recomputed by the oracle (FP64) from a periodic 9x9 window of the decoded
+    state.  Bound per population: the stored deviation is the FP32 result
+    rounded to 16 bits (stochastically: less than one unit in its last place),
+    plus 1e-5 relative for the FP32 arithmetic."""
+    w = W.large_multi_droplet(noise_amp=1e-6)
+    sim = make_sim(pkg, w, storage, shift_rho=1.0)
+    sim.step(20)
+    f0 = sim.populations()
+    sim.step(1)
+    f1 = sim.populations()
+    p, r = oracle_params(w), 4
+    shift = np.array([_shift12(wi * 1.0) for wi in O.LATTICES[9].w])
+    scale = 256.0 if storage == "fp16s" else 1.0
+    rng = np.random.default_rng(1)
+    lay = sim.layout()
+    ys = list(rng.integers(0, w.ny, 40)) + [0, 1, 2, w.ny - 1, w.ny - 2, lay["tile_rows"],
+                                           lay["tile_rows"] - 1, 3, 5, 120]
+    xs = list(rng.integers(0, w.nx, 40)) + [0, w.nx - 1, 127, 128, 129, 255, 256, w.nx - 128,
+                                           4095, 4096]
+    for y, x in zip(ys, xs):
+        fw = _window(f0, y, x, r)
+        wall = O.Wall(_window(w.phi_s, y, x, r), _window(w.psi_r, y, x, r),
+                      _window(w.psi_a, y, x, r), w.G_R, w.G_A, w.epsilon)
+        fo = O.step(p, wall, fw)[:, r, r]
+        fg = f1[:, y, x]
+        dev = np.maximum(np.abs(fo - shift), np.abs(fg - shift)) * scale
+        bound = _ulp16(dev, storage) / scale + 1e-5 * np.abs(fo)
+        assert np.all(np.abs(fg - fo) <= bound), (y, x, np.abs(fg - fo) / bound)
 
 
 def test_allocator_failure_midway_frees_what_was_obtained(pkg):
