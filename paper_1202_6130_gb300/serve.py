@@ -17,7 +17,6 @@ GPU steps.
 """
 from __future__ import annotations
 
-import math
 import time
 from collections import deque
 from concurrent.futures import ThreadPoolExecutor

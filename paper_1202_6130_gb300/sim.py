@@ -6,7 +6,6 @@ step of the update runs in the library's kernels.
 from __future__ import annotations
 
 import ctypes
-from typing import Optional
 
 import numpy as np
 

@@ -4,7 +4,6 @@ run as two gloo ranks on CPU."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

@@ -7,7 +7,6 @@ Collected last on purpose, so that a run stopping at the first failure has
 already run every other test."""
 import ctypes
 
-import numpy as np
 import pytest
 
 import workloads as W
