@@ -185,14 +185,25 @@ template <typename T> __device__ __forceinline__ T t_exp(T v);
 template <> __device__ __forceinline__ double t_exp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float t_exp<float>(float v) { return expf(v); }
 // 1 / rho.  FP64 divides exactly (quotients then divide, like the oracle);
-// FP32 arithmetic takes the hardware reciprocal (PTX rcp.approx.ftz.f32, at
-// most 1 ulp from the correctly rounded value), which every FP32 kernel shares.
+// FP32 arithmetic: the hardware reciprocal (PTX rcp.approx.ftz.f32, at most
+// 1 ulp from the correctly rounded value).
 template <typename T> __device__ __forceinline__ T t_rcp(T v);
 template <> __device__ __forceinline__ double t_rcp<double>(double v) { return 1.0 / v; }
 template <> __device__ __forceinline__ float t_rcp<float>(float v) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
   return r;
+}
+// 1 / rho as the step uses it for storage S.  FP32 storage takes the correctly
+// rounded reciprocal: the approximate one errs to one side more often than the
+// other, and on an interface that bias in u = j / rho accumulates over the
+// steps (on the 128x64 drop it doubles the density error after 1000 steps; a
+// float32 restatement shows the same 2x from a one-ulp bias).  The FP32
+// step is bound by HBM, so the few extra instructions cost nothing; 16-bit
+// storage rounds far more coarsely and keeps the cheaper approximation.
+template <typename S, typename T> __device__ __forceinline__ T rcp_node(T v) {
+  if constexpr (std::is_same<S, float>::value) return __frcp_rn(v);
+  else return t_rcp<T>(v);
 }
 template <typename T> __device__ __forceinline__ T t_fma(T a, T b, T c);
 template <> __device__ __forceinline__ double t_fma<double>(double a, double b, double c) {

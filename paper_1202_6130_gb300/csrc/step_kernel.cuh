@@ -186,8 +186,10 @@ template <int Q, typename S, int W, int NS> struct StepSmem {
   int* s_abort;
   __device__ static StepSmem carve(unsigned char* raw) {
     StepSmem v;
-    unsigned char* base =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+    // Aligned by an offset from `raw` (not through an integer cast), so that
+    // the compiler still sees shared-memory pointers and emits shared loads
+    // and stores with 32-bit addresses rather than generic ones.
+    unsigned char* base = raw + ((128u - (smem_addr(raw) & 127u)) & 127u);
     v.stages = base;
     v.bars = reinterpret_cast<uint64_t*>(base + NS * Sh::STAGE);
     v.ring = reinterpret_cast<T*>(v.bars + NS);
@@ -374,7 +376,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
       }
       T rho, jx, jy;
       node_moments<Q, T>(f, rho, jx, jy);
-      const T inv_rho = t_rcp<T>(rho);
+      const T inv_rho = rcp_node<S, T>(rho);
       const T ux = div_rho<T>(jx, rho, inv_rho);
       const T uy = div_rho<T>(jy, rho, inv_rho);
 
@@ -710,7 +712,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
             if constexpr (L::cy(i) != 0) jy = fma2(f_[i], F2::splat(T(L::cy(i))), jy);
           });
         }
-        const F2 inv_rho(t_rcp<float>(rho.x()), t_rcp<float>(rho.y()));
+        const F2 inv_rho(rcp_node<S, float>(rho.x()), rcp_node<S, float>(rho.y()));
         const F2 ux = jx * inv_rho;
         const F2 uy = jy * inv_rho;
 
