@@ -293,16 +293,19 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def measure_serving(pkg, torch, W, n: int = 32, storage: str = "fp32"):
+def measure_serving(pkg, torch, W, n: int = 300, storage: str = "fp32"):
     """Continuous-batching serving against plain sequential solves, on the
     first n requests of the Poisson stream (seed 3; sizes log-uniform 64x32 ..
     2048x1024, budgets 1k..20k steps, random wall parameters).  Two arrival
     rates: the specified 2000 req/s (a burst: throughput and queueing) and
-    10 req/s (a load the GPU sustains, so p50/p99 reflect service, not backlog).
-    Time-to-result runs from a request's arrival to its measured result
-    (contact angle or slip length) on the host."""
+    10 req/s (about 60% of what the batched loop sustains, so p50/p99 reflect
+    service rather than backlog).  Time-to-result runs from a request's
+    arrival to its measured result (contact angle or slip length) on the host.
+    The stream is capped at n requests: the full minute at 2000 req/s offers
+    about 57 times what one GPU can update in that time."""
     from paper_1202_6130_gb300 import serve
-    out = {"requests": n, "storage": storage}
+    out = {"requests": n, "storage": storage,
+           "cap": f"first {n} requests of the seed-3 stream at each rate"}
     for label, rate in (("burst_2000_per_s", 2000.0), ("sustained_10_per_s", 10.0)):
         reqs = serve.requests_from_stream(W.serving_stream(rate=rate, duration=1e9, seed=3,
                                                            max_requests=n))
@@ -369,6 +372,70 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
             "gpu_launches_batched": steps * launches}
 
 
+# Storage and lattice variants the default run measures beside the headline
+# (D2Q9 FP32), each with the number of timed steps (about 0.1-0.5 s each).
+PER_STORAGE = ((9, "fp16s", 400), (9, "bf16s", 400), (9, "fp64", 20),
+               (21, "fp32", 100), (21, "fp16s", 150), (21, "bf16s", 150))
+
+
+def roofline_of(torch, local, lattice: int, storage: str, N: int, steps: int, t: float,
+                clocks: dict) -> dict:
+    """Roofline of the fused kernel: algorithmic bytes per node update (2 Q s)
+    against the measured HBM copy rate, or for FP64 storage the executed FP64
+    flops against the DFMA peak derived from the SM count and clock."""
+    traffic = ncu_traffic(storage, lattice)
+    if storage == "fp64":
+        props = torch.cuda.get_device_properties(local)
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        fpeak = props.multi_processor_count * FP64_DFMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+        fach = FP64_FLOPS_PER_NODE[lattice] * N * steps / t / 1e12
+        return {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": fach / fpeak, "traffic": traffic,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x "
+                               f"{FP64_DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {mhz:.0f} MHz",
+                "flops_per_node": FP64_FLOPS_PER_NODE[lattice], "kernel": "lbm::step_kernel"}
+    peak, peak_kind = measured_peaks()
+    b_node = 2 * lattice * BYTES[storage]
+    achieved = b_node * N * steps / t / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+            "bytes_per_node": b_node, "kernel": "lbm::step_kernel"}
+
+
+def measure_per_storage(pkg, torch, W, local: int, nx: int, ny: int, variants=PER_STORAGE):
+    """The same workload in the other storage precisions and on D2Q21: for each,
+    warm-up launches, then timed launches of the fused step (CUDA events on the
+    library's stream, inputs far larger than L2), with the clocks sampled
+    around each timed region."""
+    N = nx * ny
+    out = {}
+    base = W.large_multi_droplet(nx=nx, ny=ny, noise_amp=0.0)
+    for lattice, storage, steps in variants:
+        base.lattice = lattice
+        sim = pkg.Simulation.from_workload(base, storage=storage)
+        stream = torch.cuda.current_stream()
+        sim.step(5)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(gpu_identifier(torch, local)) as clk:
+            ev0.record(stream)
+            sim.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        sim.sync()
+        clocks = clk.summary()
+        lay = sim.layout()
+        sim.close()
+        out[f"d2q{lattice}_{storage}"] = {
+            "lattice": f"D2Q{lattice}", "storage": storage, "dtype": DTYPE[storage],
+            "steps": steps, "ms_per_step": t / steps * 1e3, "mlups": N * steps / t / 1e6,
+            "roofline": roofline_of(torch, local, lattice, storage, N, steps, t, clocks),
+            "launch": {k: lay[k] for k in ("tile_rows", "grid_x", "grid_y", "stages")},
+            "clocks": clocks}
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -423,27 +490,9 @@ def run_gpu(args, world, rank, local):
     assert np.isfinite(outs[0]).all()
 
     # ---- roofline of the fused kernel ----------------------------------------
-    peak, peak_kind = measured_peaks()
-    b_node = 2 * args.lattice * BYTES[args.storage]
-    achieved = b_node * N * args.steps / t_local / 1e9
-    traffic = ncu_traffic(args.storage, args.lattice)
     clocks = clk.summary()
-    if args.storage == "fp64":
-        props = torch.cuda.get_device_properties(local)
-        mhz = clocks.get("sm_max_mhz") or 2070.0
-        fpeak = props.multi_processor_count * FP64_DFMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
-        fach = FP64_FLOPS_PER_NODE[args.lattice] * N * args.steps / t_local / 1e12
-        roofline = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
-                    "frac": fach / fpeak, "traffic": traffic,
-                    "peak_source": f"derived: {props.multi_processor_count} SMs x "
-                                   f"{FP64_DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {mhz:.0f} MHz",
-                    "flops_per_node": FP64_FLOPS_PER_NODE[args.lattice],
-                    "kernel": "lbm::step_kernel"}
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_node": b_node,
-                    "kernel": "lbm::step_kernel"}
+    roofline = roofline_of(torch, local, args.lattice, args.storage, N, args.steps, t_local,
+                           clocks)
     sim.close()
     if rank != 0:
         return 0
@@ -467,6 +516,8 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_per_storage:
+        line["per_storage"] = measure_per_storage(pkg, torch, W, local, nx, ny)
     if not args.no_batch:
         line["batch"] = measure_batch(pkg, torch, W)
     if not args.no_serving:
@@ -485,6 +536,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--storage", default="fp32", choices=list(DTYPE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-storage", action="store_true",
+                    help="skip the other storage precisions and D2Q21")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched parameter-sweep measurement")
     ap.add_argument("--no-serving", action="store_true",

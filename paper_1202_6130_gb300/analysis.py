@@ -83,15 +83,30 @@ class ContactAngle:
     npoints: int
 
 
+def interface_base(rho: np.ndarray, x: float, rho_mid: float) -> float:
+    """Height of the lowest crossing of ``rho_mid`` in the column nearest to x:
+    the bottom of the liquid, where the density falls towards the adsorbed
+    vapour of the solid (linear interpolation between nodes)."""
+    col = rho[:, int(round(x)) % rho.shape[1]]
+    f = col - rho_mid
+    for y in range(len(col) - 1):
+        if f[y] * f[y + 1] < 0:
+            return y + f[y] / (f[y] - f[y + 1])
+    return 0.0
+
+
 def contact_angle(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
-                  x_range=None, y_max=None) -> ContactAngle:
+                  x_range=None, y_max=None, base: str = "surface") -> ContactAngle:
     """Static contact angle of a drop resting on the bottom wall.
 
     The drop's interface is the contour rho = (rho_l + rho_v)/2; only points in
     the hydrodynamic region (phi_S < 0.01) above the bottom wall and below
-    ``y_max`` (default ny/2) are fitted.  theta = acos((y_b - y_c)/R) with y_b the
-    solid surface (phi_S = 0.5), i.e. acos(1 - h/R) with h the apex height above
-    y_b (Sec. III, static wetting)."""
+    ``y_max`` (default ny/2) are fitted.  theta = acos((y_b - y_c)/R), i.e.
+    acos(1 - h/R) with h the apex height above the base line y_b (Sec. III,
+    static wetting).  The base line: "surface" (default) the solid surface
+    phi_S = 0.5; "outer" the domain's outer boundary, the row y = 0 (one
+    reading of the Fig. 6 caption); "interface" the bottom liquid-vapour
+    interface under the drop's centre (a reading of the text of Sec. III B)."""
     ny, nx = rho.shape
     y_max = ny // 2 if y_max is None else y_max
     mask = phi_s < 0.01
@@ -104,8 +119,14 @@ def contact_angle(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float
     if len(x) < 5:
         raise ValueError("too few interface points in the hydrodynamic region")
     xc, yc, R = fit_circle(x, y)
-    col = phi_s[:, int(round(xc)) % nx]
-    yb = surface_line(col, 0.5)
+    if base == "surface":
+        yb = surface_line(phi_s[:, int(round(xc)) % nx], 0.5)
+    elif base == "outer":
+        yb = 0.0
+    elif base == "interface":
+        yb = interface_base(rho, xc, 0.5 * (rho_l + rho_v))
+    else:
+        raise ValueError(base)
     c = max(-1.0, min(1.0, (yb - yc) / R))
     return ContactAngle(math.degrees(math.acos(c)), xc, yc, R, yb, len(x))
 

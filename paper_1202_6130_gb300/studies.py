@@ -165,15 +165,21 @@ def large_precision(storages=("fp32", "fp16s", "bf16s", "fp16s-rn", "bf16s-rn"),
 PAPER_THETA = {0.0: 150.0, 0.2: 112.0, 0.5: 58.7, 0.7: 36.7, 0.8: 30.9, 0.9: 24.0}
 
 
-def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
-                      nx: int = 650, ny: int = 150, R0: float = 50.0, G_R: float = 1.33,
-                      tau: float = 1.0, solid_rows: int = 1):
-    """The paper's fluid and walls: D2Q21, Eq. EOS (theta_V = theta/4, theta_U =
-    -theta/4, theta_L = theta, rho_1 = 0.222, rho_2 = 0.869) with G = -1/theta,
-    projection on, wall functions from the Appendix filter of a solid slab
-    (psi_R = G^(5), psi_A = G^(22) - G^(5), phi_S = G^(22), epsilon = 1).  A
-    disc of area pi R0^2 starts tangent to the wall; the static angle is fitted
-    as for the other drops.  Readings (1/theta in the force, the sign of
+BASES = ("surface", "outer", "interface")
+
+
+def paper_drops(cases, steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
+                nx: int = 650, ny: int = 150, G_R: float = 1.33, tau: float = 1.0,
+                solid_rows: int = 1):
+    """Sessile drops of the paper's fluid and walls, one per (R0, G_A) in
+    ``cases``, advanced together in one batch: D2Q21, Eq. EOS (theta_V =
+    theta/4, theta_U = -theta/4, theta_L = theta, rho_1 = 0.222, rho_2 =
+    0.869) with G = -1/theta, projection on, wall functions from the Appendix
+    filter of a solid slab (psi_R = G^(5), psi_A = G^(22) - G^(5), phi_S =
+    G^(22), epsilon = 1).  A disc of area pi R0^2 starts tangent to the wall.
+    Per case: the static angle on each base line of ``analysis.contact_angle``
+    (the solid surface, the domain's outer boundary, the bottom liquid-vapour
+    interface) and its history.  Readings (1/theta in the force, the sign of
     psi_FS) are the ones the oracle uses."""
     import workloads as W
     th = 2.0 / 3.0
@@ -182,38 +188,58 @@ def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "f
     phi, pr, pa = wall_gaussian_filter(solid, lattice=21, n_rep=5, n_att=22)
     yb = analysis.surface_line(phi[:, 0], 0.5)
     rho_l, rho_v = 1.0, 0.1
-    sims, meta = [], []
-    for ga in PAPER_THETA:
+    sims = []
+    for R0, ga in cases:
         rho = W.droplet_density(nx, ny, [(nx / 2.0, yb + R0)], [R0], rho_l, rho_v, 3.0)
         s = Simulation(nx, ny, lattice=21, storage=storage, tau=tau, G=-1.0 / th, psi_kind=1,
                        project=True, eos=(0.25 * th, -0.25 * th, th, 0.222, 0.869))
         s.set_wall(phi, pr, pa, G_R, ga, 1.0)
         s.set_equilibrium(rho)
         sims.append(s)
-        meta.append(ga)
-    hist = {ga: [] for ga in meta}
+    hist = [[] for _ in cases]
 
     def record(done):
-        for s, ga in zip(sims, meta):
-            rho, ux, uy = s.moments()
-            try:
-                c = analysis.contact_angle(rho, phi, rho_l, rho_v, y_max=ny - 10)
-                hist[ga].append((done, c.theta_deg, c.R))
-            except Exception:
-                hist[ga].append((done, float("nan"), float("nan")))
+        for k, s in enumerate(sims):
+            rho, _, _ = s.moments()
+            row = [done]
+            for base in BASES:
+                try:
+                    row.append(analysis.contact_angle(rho, phi, rho_l, rho_v, y_max=ny - 10,
+                                                      base=base).theta_deg)
+                except Exception:
+                    row.append(float("nan"))
+            hist[k].append(tuple(row))
 
     t0 = time.perf_counter()
     _run_batch(sims, steps, chunk, record)
-    out = {"nx": nx, "ny": ny, "R0": R0, "G_R": G_R, "steps": steps, "storage": storage,
-           "wall_s": time.perf_counter() - t0, "y_surface": yb, "rows": []}
-    for s, ga in zip(sims, meta):
-        th_end = hist[ga][-1][1]
-        out["rows"].append({"G_A": ga, "theta_deg": th_end, "paper_theta_deg": PAPER_THETA[ga],
-                            "diff_deg": th_end - PAPER_THETA[ga],
-                            "theta_change_last_chunk_deg":
-                                th_end - hist[ga][-2][1] if len(hist[ga]) > 1 else float("nan"),
-                            "history": hist[ga]})
+    wall = time.perf_counter() - t0
+    rows = []
+    for (R0, ga), h in zip(cases, hist):
+        last, prev = h[-1], h[-2] if len(h) > 1 else h[-1]
+        rows.append({"R0": R0, "G_A": ga,
+                     "theta_deg": dict(zip(BASES, last[1:])),
+                     "theta_change_last_chunk_deg": last[1] - prev[1], "history": h})
+    for s in sims:
         s.close()
+    return {"nx": nx, "ny": ny, "G_R": G_R, "steps": steps, "storage": storage,
+            "wall_s": wall, "y_surface": yb, "rows": rows}
+
+
+def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
+                      nx: int = 650, ny: int = 150, R0: float = 50.0, G_R: float = 1.33,
+                      tau: float = 1.0, solid_rows: int = 1, R0_others=(30.0, 65.0)):
+    """The static angle against G_A at G_R = 1.33 (Sec. III B, Figs. 6-7) next
+    to the printed angles, at R0 = ``R0``; and, for the angles the domain
+    holds at every size (G_A = 0-0.7), at the drop sizes ``R0_others`` too
+    (the paper reports no significant dependence on R0 = 30-80)."""
+    cases = [(R0, ga) for ga in PAPER_THETA]
+    cases += [(r, ga) for r in R0_others for ga in PAPER_THETA if ga <= 0.7]
+    out = paper_drops(cases, steps=steps, chunk=chunk, storage=storage, nx=nx, ny=ny, G_R=G_R,
+                      tau=tau, solid_rows=solid_rows)
+    for r in out["rows"]:
+        r["paper_theta_deg"] = PAPER_THETA[r["G_A"]]
+        r["diff_deg"] = r["theta_deg"]["surface"] - PAPER_THETA[r["G_A"]]
+    out["R0"] = R0
     return out
 
 

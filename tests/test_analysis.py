@@ -68,3 +68,25 @@ def test_dynamic_angles_of_two_joined_circular_arcs():
     for shift in (0, 320):
         d = A.dynamic_angles(np.roll(dens, shift, axis=1), phi, 1.0, 0.1)
         assert abs(d.theta_adv_deg - 70.0) < 1.0 and abs(d.theta_rec_deg - 50.0) < 1.0, d
+
+
+def test_contact_angle_base_line_readings():
+    """The three base lines of the static angle on a cap whose liquid ends in
+    a sharp step at y = 4 (a stand-in for the liquid-vapour interface at the
+    bottom of a drop): "surface" (phi_S = 0.5), "outer" (the row y = 0) and
+    "interface" (the step), each acos((y_b - y_c) / R) of the same circle."""
+    nx, ny = 400, 240
+    phi, _, _ = W.wall_core_tail(W.wall_distance_slab(nx, ny), 3.0)
+    R, yc = 60.0, -10.0
+    rho = W.droplet_density(nx, ny, [(200.0, yc)], [R], 2.0, 0.1, 2.0)
+    rho[:4, :] = 0.1
+    rho[4, :] = np.where(rho[4, :] > 1.05, 1.05 + 0.5 * (rho[4, :] - 1.05), rho[4, :])
+    ys = {"surface": A.surface_line(phi[:, 200], 0.5), "outer": 0.0}
+    col = rho[:, 200] - 1.05
+    k = int(np.nonzero(col[:-1] * col[1:] < 0)[0][0])
+    ys["interface"] = k + col[k] / (col[k] - col[k + 1])
+    for base, yb in ys.items():
+        ca = A.contact_angle(rho, phi, 2.0, 0.1, base=base)
+        want = math.degrees(math.acos((yb - yc) / R))
+        assert abs(ca.theta_deg - want) < 0.3, (base, ca.theta_deg, want)
+        assert abs(ca.y_base - yb) < 1e-12

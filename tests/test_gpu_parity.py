@@ -190,12 +190,15 @@ PAIRED_CASES = [dict(nx=67, ny=35, tile_rows=5), dict(nx=1, ny=16, tile_rows=4),
 
 @pytest.mark.parametrize("case", PAIRED_CASES, ids=lambda c: "x".join(map(str, (c["nx"], c["ny"])))
                          + f"_q{c.get('lattice', 9)}")
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16s", 2e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16s", 8e-3), ("bf16s", 6.4e-2)])
 def test_paired_path_ragged_sizes_match_oracle(pkg, case, storage, tol):
     """The two-nodes-per-thread path (D2Q9 in FP32 and 16-bit storage, D2Q21 in
     16-bit storage; D2Q21 FP32 runs one node per thread) on odd widths (a lone
-    last column), a one-column and a one-row lattice, many tiles: FP32 within
-    1e-5 of the oracle after 40 steps, 16-bit storage within its rounding."""
+    last column), a one-column and a one-row lattice, many tiles, after 40
+    steps.  FP32: 1e-5 in rho and u.  16-bit storage: rho within 8e-3 (FP16S,
+    about three times the largest error over these cases) and eight times that
+    for BF16S (three fewer significant bits); u within three times the rho
+    bound, relative to its maximum."""
     case = dict(case)
     tr = case.pop("tile_rows")
     w = _small_case(**case)
@@ -203,7 +206,8 @@ def test_paired_path_ragged_sizes_match_oracle(pkg, case, storage, tol):
     sim = make_sim(pkg, w, storage, tile_rows=tr)
     sim.step(40)
     e_rho, e_u, _ = rel_errors(sim.moments(), (rho, ux, uy))
-    assert e_rho <= tol and e_u <= tol * 10, (e_rho, e_u)
+    u_tol = tol if storage == "fp32" else 3 * tol
+    assert e_rho <= tol and e_u <= u_tol, (e_rho, e_u)
 
 
 @pytest.mark.parametrize("lattice", [9, 21])
@@ -378,6 +382,42 @@ def test_full_size_16bit_sampled_nodes_match_oracle(pkg, storage):
                                            lay["tile_rows"] - 1, 3, 5, 120]
     xs = list(rng.integers(0, w.nx, 40)) + [0, w.nx - 1, 127, 128, 129, 255, 256, w.nx - 128,
                                            4095, 4096]
+    for y, x in zip(ys, xs):
+        fw = _window(f0, y, x, r)
+        wall = O.Wall(_window(w.phi_s, y, x, r), _window(w.psi_r, y, x, r),
+                      _window(w.psi_a, y, x, r), w.G_R, w.G_A, w.epsilon)
+        fo = O.step(p, wall, fw)[:, r, r]
+        fg = f1[:, y, x]
+        dev = np.maximum(np.abs(fo - shift), np.abs(fg - shift)) * scale
+        bound = _ulp16(dev, storage) / scale + 1e-5 * np.abs(fo)
+        assert np.all(np.abs(fg - fo) <= bound), (y, x, np.abs(fg - fo) / bound)
+
+
+@pytest.mark.parametrize("storage", ["fp16s", "bf16s"])
+def test_d2q21_16bit_sampled_nodes_match_oracle(pkg, storage):
+    """One D2Q21 step in 16-bit storage on the multi-droplet lattice at
+    4096x2048, in the launch shape of the D2Q21 benchmark (node pairs, 48-row
+    segments), after 20 warm-up steps; sampled nodes recomputed by the oracle
+    (FP64) from a periodic 15x15 window of the decoded state (the step's reach
+    is 2R = 6).  Same bound per population as the D2Q9 test: less than one unit
+    in the last place of the stored 16-bit deviation plus 1e-5 relative."""
+    w = W.large_multi_droplet(nx=4096, ny=2048, noise_amp=0.0)
+    w.lattice = 21
+    sim = make_sim(pkg, w, storage, shift_rho=1.0)
+    sim.step(20)
+    f0 = sim.populations()
+    sim.step(1)
+    f1 = sim.populations()
+    p, r = oracle_params(w), 7
+    shift = np.array([_shift12(wi * 1.0) for wi in O.LATTICES[21].w])
+    scale = 256.0 if storage == "fp16s" else 1.0
+    rng = np.random.default_rng(2)
+    lay = sim.layout()
+    L = lay["tile_rows"]
+    ys = list(rng.integers(0, w.ny, 30)) + [0, 1, 2, 3, 5, w.ny - 1, w.ny - 3, L, L - 1, L + 2,
+                                           2 * L - 3, 60, 100]
+    xs = list(rng.integers(0, w.nx, 30)) + [0, w.nx - 1, 126, 127, 128, 130, 255, 256, w.nx - 129,
+                                           2047, 2048, 3, w.nx - 3]
     for y, x in zip(ys, xs):
         fw = _window(f0, y, x, r)
         wall = O.Wall(_window(w.phi_s, y, x, r), _window(w.psi_r, y, x, r),
