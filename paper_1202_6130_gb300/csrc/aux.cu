@@ -41,7 +41,6 @@ __global__ void encode_kernel(const double* __restrict__ f, S* __restrict__ buf,
   using L = Lattice<Q>;
   constexpr int R = L::R;
   constexpr int GX = ghost_x<S, R>(), GY = ghost_y<R>();
-  using T = typename Codec<S>::T;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
@@ -50,7 +49,7 @@ __global__ void encode_kernel(const double* __restrict__ f, S* __restrict__ buf,
     constexpr int i = decltype(ic)::value;
     const int xs = wrap(x + L::cx(i), nx), ys = wrap(y + L::cy(i), ny);
     const double v = f[i * N + (int64_t)ys * nx + xs];
-    const S e = Codec<S>::enc((T)v, (T)storage_shift(L::w(i), rho_s));
+    const S e = Codec<S>::enc_host(v, L::w(i) * rho_s);
     store_images<S, GX, GY>(buf, plane, pitch, Planes<Q>::template plane<i>, x, y, nx, ny, e);
   });
 }
@@ -64,7 +63,6 @@ __global__ void equilibrium_kernel(const double* __restrict__ rho, const double*
   using E = EqConst<Q>;
   constexpr int R = L::R;
   constexpr int GX = ghost_x<S, R>(), GY = ghost_y<R>();
-  using T = typename Codec<S>::T;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
@@ -76,7 +74,7 @@ __global__ void equilibrium_kernel(const double* __restrict__ rho, const double*
     const double usq = (vx * vx + vy * vy) * E::inv_2theta;
     double v = feq<Q, double>(i, r, vx, vy, usq);
     if (dfi) v = v + dfi[i * N + m];
-    const S e = Codec<S>::enc((T)v, (T)storage_shift(L::w(i), rho_s));
+    const S e = Codec<S>::enc_host(v, L::w(i) * rho_s);
     store_images<S, GX, GY>(buf, plane, pitch, Planes<Q>::template plane<i>, x, y, nx, ny, e);
   });
 }
@@ -87,7 +85,6 @@ __global__ void decode_kernel(const S* __restrict__ buf, double* __restrict__ f,
   using L = Lattice<Q>;
   constexpr int R = L::R;
   constexpr int GX = ghost_x<S, R>(), GY = ghost_y<R>();
-  using T = typename Codec<S>::T;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= (int64_t)nx * ny) return;
   const int x = (int)(n % nx), y = (int)(n / nx);
@@ -97,7 +94,7 @@ __global__ void decode_kernel(const S* __restrict__ buf, double* __restrict__ f,
     // f_i(x) = P_i(x - c_i); the ghost frame makes the source in-bounds.
     const int64_t src = Planes<Q>::template plane<i> * plane +
                         (int64_t)(y - L::cy(i) + GY) * pitch + (x - L::cx(i) + GX);
-    f[i * N + n] = (double)Codec<S>::dec(buf[src], (T)storage_shift(L::w(i), rho_s));
+    f[i * N + n] = Codec<S>::dec_host(buf[src], L::w(i) * rho_s);
   });
 }
 

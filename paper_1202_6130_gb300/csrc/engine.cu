@@ -263,12 +263,7 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   P.bfx = (T)p.body_force[0];
   P.bfy = (T)p.body_force[1];
   P.rho_s = (T)c->rho_s;
-  for (int i = 0; i < kMaxQ; ++i) P.shift[i] = P.enc_add[i] = 0.0f;
-  for (int i = 0; i < c->Q; ++i) {
-    P.shift[i] = storage_shift(c->Q == 9 ? Lattice<9>::w(i) : Lattice<21>::w(i), c->rho_s);
-    // exact: a 12-bit shift times a power of two
-    P.enc_add[i] = c->p.storage == LBM_FP16S ? -kHalfScale * P.shift[i] : -P.shift[i];
-  }
+  P.neg_omega_rho_s = (T)(-c->rho_s / p.tau);
   P.psi_kind = p.psi_kind;
   P.project = p.project;
   return P;
@@ -348,7 +343,7 @@ int set_shift_from_rho(lbm_ctx* c, const double* d_rho) {
     return LBM_OK;
   }
   if (c->p.shift_rho > 0.0) {
-    c->rho_s = c->p.shift_rho;
+    c->rho_s = storage_rho_s(c->p.shift_rho);
     return LBM_OK;
   }
   const int64_t N = (int64_t)c->p.nx * c->p.ny;
@@ -356,7 +351,7 @@ int set_shift_from_rho(lbm_ctx* c, const double* d_rho) {
   double h[3];
   CK(c, cudaMemcpyAsync(h, c->d_out3, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  c->rho_s = h[0] / (double)N;
+  c->rho_s = storage_rho_s(h[0] / (double)N);
   return LBM_OK;
 }
 

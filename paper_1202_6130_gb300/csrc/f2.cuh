@@ -46,32 +46,23 @@ template <int CX, int CY> __device__ __forceinline__ F2 cdot2(F2 ux, F2 uy) {
   else return cmul2<CX>(ux) + cmul2<CY>(uy);
 }
 
-// Two adjacent stored values as an F2.
+// Two adjacent stored values as an F2 (load, load1) and back (store_rn,
+// store_sr): FP32 storage moves f; FP16S / BF16S move the scaled deviation h
+// (see the codecs in node.cuh), converted exactly to FP32 and rounded back to
+// 16 bits, to nearest-even or stochastically.
 template <typename S> struct Pair;
 template <> struct Pair<__half> {
   using Raw = __half2;
   __device__ __forceinline__ static __half lane(Raw r, int e) { return e ? __high2half(r) : __low2half(r); }
-  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) {
-    return fma2(F2(__half22float2(r)), F2::splat(kHalfInvScale), wrs);
+  __device__ __forceinline__ static F2 load(Raw r) { return F2(__half22float2(r)); }
+  __device__ __forceinline__ static F2 load1(__half a, __half b) {
+    return F2(__half2float(a), __half2float(b));
   }
-  __device__ __forceinline__ static F2 dec1(__half a, __half b, F2 wrs) {
-    return fma2(F2(__half2float(a), __half2float(b)), F2::splat(kHalfInvScale), wrs);
-  }
-  // add = -2^8 shift: (f - shift) * 2^8 as one fused operation.  Exact
-  // scaling by a power of two commutes with the rounding, so it equals
-  // Codec<__half>'s value.
-  __device__ __forceinline__ static F2 scaled(F2 f, F2 add) {
-    return fma2(f, F2::splat(kHalfScale), add);
-  }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 add) {
-    const F2 d = scaled(f, add);
-    return __floats2half2_rn(d.x(), d.y());
-  }
-  // Stochastic rounding of both lanes from one random word r (see
-  // Codec<__half>::enc_sr; first node in the low half).
-  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 add, uint32_t r) {
-    const F2 d = scaled(f, add);
-    const uint32_t u = cvt_rs_f16x2(d.y(), d.x(), r);
+  __device__ __forceinline__ static Raw store_rn(F2 h) { return __floats2half2_rn(h.x(), h.y()); }
+  // Stochastic rounding of both lanes from one random word r (first node in
+  // the low half).
+  __device__ __forceinline__ static Raw store_sr(F2 h, uint32_t r) {
+    const uint32_t u = cvt_rs_f16x2(h.y(), h.x(), r);
     Raw out;
     static_assert(sizeof(out) == sizeof(u), "half2 is 32 bits");
     memcpy(&out, &u, sizeof u);
@@ -83,20 +74,13 @@ template <> struct Pair<__nv_bfloat16> {
   __device__ __forceinline__ static __nv_bfloat16 lane(Raw r, int e) {
     return e ? __high2bfloat16(r) : __low2bfloat16(r);
   }
-  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(__bfloat1622float2(r)) + wrs; }
-  __device__ __forceinline__ static F2 dec1(__nv_bfloat16 a, __nv_bfloat16 b, F2 wrs) {
-    return F2(__bfloat162float(a), __bfloat162float(b)) + wrs;
+  __device__ __forceinline__ static F2 load(Raw r) { return F2(__bfloat1622float2(r)); }
+  __device__ __forceinline__ static F2 load1(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return F2(__bfloat162float(a), __bfloat162float(b));
   }
-  // add = -shift.
-  __device__ __forceinline__ static Raw enc(F2 f, F2 add) {
-    const F2 d = f + add;
-    return __floats2bfloat162_rn(d.x(), d.y());
-  }
-  // Stochastic rounding of both lanes from one random word r (see
-  // Codec<__nv_bfloat16>::enc_sr; first node in the low half).
-  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 add, uint32_t r) {
-    const F2 d = f + add;
-    const uint32_t u = cvt_rs_bf16x2(d.y(), d.x(), r);
+  __device__ __forceinline__ static Raw store_rn(F2 h) { return __floats2bfloat162_rn(h.x(), h.y()); }
+  __device__ __forceinline__ static Raw store_sr(F2 h, uint32_t r) {
+    const uint32_t u = cvt_rs_bf16x2(h.y(), h.x(), r);
     Raw out;
     static_assert(sizeof(out) == sizeof(u), "bfloat162 is 32 bits");
     memcpy(&out, &u, sizeof u);
@@ -106,10 +90,10 @@ template <> struct Pair<__nv_bfloat16> {
 template <> struct Pair<float> {
   using Raw = float2;
   __device__ __forceinline__ static float lane(Raw r, int e) { return e ? r.y : r.x; }
-  __device__ __forceinline__ static F2 dec(Raw r, F2 wrs) { return F2(r); }
-  __device__ __forceinline__ static Raw enc(F2 f, F2 wrs) { return f.v; }
-  __device__ __forceinline__ static Raw enc_sr(F2 f, F2 wrs, uint32_t) { return f.v; }
-  __device__ __forceinline__ static F2 dec1(float a, float b, F2 wrs) { return F2(a, b); }
+  __device__ __forceinline__ static F2 load(Raw r) { return F2(r); }
+  __device__ __forceinline__ static F2 load1(float a, float b) { return F2(a, b); }
+  __device__ __forceinline__ static Raw store_rn(F2 f) { return f.v; }
+  __device__ __forceinline__ static Raw store_sr(F2 f, uint32_t) { return f.v; }
 };
 
 }  // namespace lbm

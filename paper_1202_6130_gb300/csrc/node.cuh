@@ -17,16 +17,23 @@ namespace lbm {
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  FP64 / FP32 store f directly.  FP16S / BF16S store the
-// deviation f_i - shift_i in 16 bits (FP16S scaled by kHalfScale = 2^8, so that
-// deviations down to 2.4e-7 stay in the normal range of binary16, and up to
-// 256 fit) and compute in FP32.  enc rounds to nearest-even; enc_sr rounds
-// stochastically: random bits are added below the kept mantissa of the FP32
-// value and the sum is truncated, so the stored value rounds up with
-// probability equal to the discarded fraction and its expectation is the
-// FP32 value (subnormal results included; overflow gives inf).  Round-to-
-// nearest loses every per-step increment smaller than half a unit in the last
-// place (a body force of 1e-6 adds about 3e-7 per population); the stochastic
-// version keeps them on average.
+// scaled deviation h_i = sigma (f_i - w_i rho_s) from the shift w_i rho_s in 16
+// bits, with sigma = kHalfScale = 2^8 for FP16S (deviations down to 2.4e-7
+// stay in the normal range of binary16, and up to 256 fit) and sigma = 1 for
+// BF16S.  The step computes on h itself in FP32: rho = sum_i h_i / sigma +
+// rho_s (the weights sum to one), j = sum_i h_i c_i / sigma (the shift carries
+// no momentum), and the collision and the projection map deviations to
+// deviations, so no per-population shift is ever added or subtracted in FP32.
+// The conversion to 16 bits rounds to nearest-even or stochastically: random
+// bits are added below the kept mantissa of the FP32 value and the sum is
+// truncated, so the stored value rounds up with probability equal to the
+// discarded fraction and its expectation is the FP32 value (subnormal results
+// included; overflow gives inf).  Round-to-nearest loses every per-step
+// increment smaller than half a unit in the last place (a body force of 1e-6
+// adds about 3e-7 per population); the stochastic version keeps them on
+// average.  Set-up and read-out convert between f and h in FP64 (enc_host,
+// dec_host), with the shift w_i rho_s formed in FP64 from the same rho_s the
+// step uses.
 // ---------------------------------------------------------------------------
 
 // Stochastic-rounding conversions of the sm_100 family: two FP32 values to a
@@ -44,77 +51,75 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r
   return u;
 }
 
+constexpr float kHalfScale = 256.0f;
+constexpr float kHalfInvScale = 1.0f / 256.0f;
+
+// load: the stored value in the compute type (f, or the scaled deviation h);
+// store_rn / store_sr: back to storage (h rounded to 16 bits for FP16S and
+// BF16S); enc_host / dec_host: FP64 f <-> storage given the shift w_i rho_s.
 template <typename S> struct Codec;
 
 template <> struct Codec<double> {
   using T = double;
   static constexpr bool kShifted = false;
-  __device__ __forceinline__ static T dec(double v, T) { return v; }
-  __device__ __forceinline__ static double enc(T f, T) { return f; }
-  __device__ __forceinline__ static double enc_sr(T f, T, uint32_t) { return f; }
+  static constexpr double kScale = 1.0;
+  __device__ __forceinline__ static T load(double v) { return v; }
+  __device__ __forceinline__ static double store_rn(T v) { return v; }
+  __device__ __forceinline__ static double store_sr(T v, uint32_t) { return v; }
+  __host__ __device__ static double enc_host(double f, double) { return f; }
+  __host__ __device__ static double dec_host(double v, double) { return v; }
 };
 
 template <> struct Codec<float> {
   using T = float;
   static constexpr bool kShifted = false;
-  __device__ __forceinline__ static T dec(float v, T) { return v; }
-  __device__ __forceinline__ static float enc(T f, T) { return f; }
-  __device__ __forceinline__ static float enc_sr(T f, T, uint32_t) { return f; }
+  static constexpr float kScale = 1.0f;
+  __device__ __forceinline__ static T load(float v) { return v; }
+  __device__ __forceinline__ static float store_rn(T v) { return v; }
+  __device__ __forceinline__ static float store_sr(T v, uint32_t) { return v; }
+  __host__ __device__ static float enc_host(double f, double) { return (float)f; }
+  __host__ __device__ static double dec_host(float v, double) { return (double)v; }
 };
-
-constexpr float kHalfScale = 256.0f;
-constexpr float kHalfInvScale = 1.0f / 256.0f;
 
 template <> struct Codec<__half> {
   using T = float;
   static constexpr bool kShifted = true;
-  __device__ __forceinline__ static T dec(__half v, T wrs) {
-    return fmaf(__half2float(v), kHalfInvScale, wrs);
-  }
-  // (f - wrs) * 2^8 with explicitly rounded operations: no kernel may contract
-  // it differently (a product w_i rho_s hoisted in one kernel and fused in
-  // another would change the last bit).
-  __device__ __forceinline__ static float scaled(T f, T wrs) {
-    return __fmul_rn(__fsub_rn(f, wrs), kHalfScale);
-  }
-  __device__ __forceinline__ static __half enc(T f, T wrs) { return __float2half_rn(scaled(f, wrs)); }
+  static constexpr float kScale = kHalfScale;
+  __device__ __forceinline__ static T load(__half v) { return __half2float(v); }
+  __device__ __forceinline__ static __half store_rn(T h) { return __float2half_rn(h); }
   // r: random word (bits 12..0 are used).
-  __device__ __forceinline__ static __half enc_sr(T f, T wrs, uint32_t r) {
-    return __ushort_as_half((unsigned short)(cvt_rs_f16x2(0.0f, scaled(f, wrs), r) & 0xFFFFu));
+  __device__ __forceinline__ static __half store_sr(T h, uint32_t r) {
+    return __ushort_as_half((unsigned short)(cvt_rs_f16x2(0.0f, h, r) & 0xFFFFu));
+  }
+  __device__ static __half enc_host(double f, double shift) {
+    return __double2half((f - shift) * (double)kHalfScale);
+  }
+  __device__ static double dec_host(__half v, double shift) {
+    return (double)__half2float(v) * (double)kHalfInvScale + shift;
   }
 };
 
 template <> struct Codec<__nv_bfloat16> {
   using T = float;
   static constexpr bool kShifted = true;
-  // Explicitly rounded add / subtract, as for FP16S.
-  __device__ __forceinline__ static T dec(__nv_bfloat16 v, T wrs) {
-    return __fadd_rn(__bfloat162float(v), wrs);
-  }
-  __device__ __forceinline__ static __nv_bfloat16 enc(T f, T wrs) {
-    return __float2bfloat16_rn(__fsub_rn(f, wrs));
-  }
+  static constexpr float kScale = 1.0f;
+  __device__ __forceinline__ static T load(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static __nv_bfloat16 store_rn(T h) { return __float2bfloat16_rn(h); }
   // r: random word (bits 15..0 are used).
-  __device__ __forceinline__ static __nv_bfloat16 enc_sr(T f, T wrs, uint32_t r) {
-    return __ushort_as_bfloat16(
-        (unsigned short)(cvt_rs_bf16x2(0.0f, __fsub_rn(f, wrs), r) & 0xFFFFu));
+  __device__ __forceinline__ static __nv_bfloat16 store_sr(T h, uint32_t r) {
+    return __ushort_as_bfloat16((unsigned short)(cvt_rs_bf16x2(0.0f, h, r) & 0xFFFFu));
+  }
+  __device__ static __nv_bfloat16 enc_host(double f, double shift) {
+    return __double2bfloat16(f - shift);
+  }
+  __device__ static double dec_host(__nv_bfloat16 v, double shift) {
+    return (double)__bfloat162float(v) + shift;
   }
 };
 
-// Storage shift of population i for FP16S / BF16S: w_i rho_s rounded to 12
-// significant bits.  Any constant serves as the shift, as long as encode and
-// decode use the same one; a short mantissa makes the FP32 decode dev + shift
-// and the encode f - shift exact in nearly all cases.  With the full product
-// w_i rho_s (w_i = 1/9, 1/36, ...) the decode rounded every stored value of a
-// population the same way, which drifted the mass by about 1e-8 per node and
-// step.  Computed in FP64 with exact scalings, so host and device agree.
-__host__ __device__ inline float storage_shift(double w, double rho_s) {
-  const double x = w * rho_s;
-  if (!(x > 0.0)) return 0.0f;
-  int e = 0;
-  (void)frexp(x, &e);
-  return (float)ldexp(nearbyint(ldexp(x, 12 - e)), e - 12);
-}
+// rho_s as the step uses it: the FP32 value of the shift density, so that the
+// FP64 shift w_i rho_s of set-up and read-out matches the step's arithmetic.
+__host__ __device__ inline double storage_rho_s(double rho_s) { return (double)(float)rho_s; }
 
 constexpr int kMaxQ = 21;
 
@@ -161,11 +166,8 @@ template <typename T> struct Physics {
   T inv_rho0;        // 1 / rho0
   T eos_tv, eos_tu, eos_tl, eos_r1, eos_r2, eos_p1, eos_p2;
   T bfx, bfy;        // body-force density
-  T rho_s;           // FP16S / BF16S shift density
-  float shift[kMaxQ];  // FP16S / BF16S: storage_shift(w_i, rho_s) per population
-  // What the paired encoder adds after its scaling: -2^8 shift_i (FP16S) or
-  // -shift_i (BF16S), so that the encode is one fused operation.
-  float enc_add[kMaxQ];
+  T rho_s;           // FP16S / BF16S shift density (stored h_i = sigma (f_i - w_i rho_s))
+  T neg_omega_rho_s; // -rho_s / tau: the shift's share of the collision of h
   int32_t psi_kind;  // 0 exp, 1 EOS
   int32_t project;   // projection step on/off
 };
@@ -217,14 +219,18 @@ template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return 
 template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
 
 // psi(rho): exponential (Shan-Chen) or sqrt(2 [rho theta - p_EOS(rho)]) with the
-// piecewise-linear Eq. EOS.
-template <int Q, typename T>
+// piecewise-linear Eq. EOS.  KIND: the kind if known at compile time (0
+// exponential, 1 EOS), else -1 (P.psi_kind decides).  FAST: the exponential
+// by the hardware base-2 exponential (__expf: a few ulp, where expf is within
+// one); used with 16-bit storage, whose rounding is about 2^-11 of a deviation.
+template <int Q, typename T, int KIND = -1, bool FAST = false>
 __device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
-  if (P.psi_kind == 0) {
+  if (KIND == 0 || (KIND < 0 && P.psi_kind == 0)) {
     // FP64 divides like the oracle; FP32 multiplies by the reciprocal (exact
     // for the usual rho0 = 1).
     const T arg = sizeof(T) == 8 ? -rho / P.rho0 : -rho * P.inv_rho0;
-    return P.rho0 * (T(1) - t_exp<T>(arg));
+    if constexpr (FAST && sizeof(T) == 4) return P.rho0 * (T(1) - __expf(arg));
+    else return P.rho0 * (T(1) - t_exp<T>(arg));
   }
   constexpr T theta = T(Lattice<Q>::THETA);
   T p;

@@ -6,14 +6,39 @@
 
 namespace lbm {
 
-template <int Q, typename S, int MODE>
+template <int Q, typename S, int MODE, int FL>
 static cudaError_t prepare_kernel() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   static cudaError_t once = cudaFuncSetAttribute(
-      step_kernel<Q, S, Cfg::W, Cfg::NS, MODE, Cfg::MINB>,
+      step_kernel<Q, S, Cfg::W, Cfg::NS, MODE, Cfg::MINB, FL>,
       cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   return once;
+}
+
+// The fused step as a programmatic dependent launch: the step may begin
+// launching while the previous kernel in the stream drains (the kernel waits
+// before touching global memory).
+template <int Q, typename S, int FL>
+static cudaError_t launch_step_pdl(const PopMaps& src, const CUtensorMap& flags,
+                                   const StepArgs<typename Codec<S>::T, S>& a, dim3 grid,
+                                   cudaStream_t stream) {
+  using Cfg = StepConfig<Q, S>;
+  using Sh = ConfigShape<Q, S>;
+  cudaError_t e;
+  if ((e = prepare_kernel<Q, S, kModeStep, FL>()) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(Sh::NT);
+  cfg.dynamicSmemBytes = Sh::SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB, FL>,
+                            src, flags, a);
 }
 
 template <int Q, typename S>
@@ -24,26 +49,16 @@ cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
   using Sh = ConfigShape<Q, S>;
   cudaError_t e;
   if (mode == kModeStep) {
-    if ((e = prepare_kernel<Q, S, kModeStep>()) != cudaSuccess) return e;
-    // Programmatic dependent launch: the step may begin launching while the
-    // previous kernel in the stream drains (the kernel waits before touching
-    // global memory).
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(Sh::NT);
-    cfg.dynamicSmemBytes = Sh::SMEM;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, src,
-                           flags, a);
+    // The common settings (exponential psi, no projection, stochastic
+    // rounding of 16-bit storage) run a kernel with them fixed at compile time.
+    const bool plain = a.phys.psi_kind == 0 && !a.phys.project &&
+                       (a.stochastic || !Codec<S>::kShifted);
+    e = plain ? launch_step_pdl<Q, S, kFlExpPlain>(src, flags, a, grid, stream)
+              : launch_step_pdl<Q, S, kFlRuntime>(src, flags, a, grid, stream);
     if (e != cudaSuccess) return e;
   } else {
-    if ((e = prepare_kernel<Q, S, kModeMoments>()) != cudaSuccess) return e;
-    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments, Cfg::MINB>
+    if ((e = prepare_kernel<Q, S, kModeMoments, kFlRuntime>()) != cudaSuccess) return e;
+    step_kernel<Q, S, Cfg::W, Cfg::NS, kModeMoments, Cfg::MINB, kFlRuntime>
         <<<grid, Sh::NT, Sh::SMEM, stream>>>(src, flags, a);
   }
   return cudaGetLastError();
@@ -52,11 +67,11 @@ cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
 template <int Q, typename S> int step_ctas_per_sm() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
-  if (prepare_kernel<Q, S, kModeStep>() != cudaSuccess) return 0;
+  if (prepare_kernel<Q, S, kModeStep, kFlRuntime>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB>, Sh::NT, Sh::SMEM) !=
-      cudaSuccess)
+          &n, step_kernel<Q, S, Cfg::W, Cfg::NS, kModeStep, Cfg::MINB, kFlRuntime>, Sh::NT,
+          Sh::SMEM) != cudaSuccess)
     return 0;
   return n;
 }

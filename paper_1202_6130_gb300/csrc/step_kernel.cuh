@@ -45,6 +45,13 @@ enum StepMode : int {
   kModeMoments = 1,   // write rho and u = (j + F/2) / rho (FP64) instead
 };
 
+// Which run-time switches of the update are fixed at compile time:
+// kFlRuntime reads psi_kind, project and the rounding mode from the
+// arguments; kFlExpPlain is the exponential pseudo-potential without the
+// projection step, with stochastic rounding for 16-bit storage (the other
+// settings run the kFlRuntime kernel).  Both give the same bits.
+enum StepFlags : int { kFlRuntime = 0, kFlExpPlain = 1 };
+
 template <typename T, typename S> struct StepArgs {
   Physics<T> phys;
   WallFields<T> wall;
@@ -69,10 +76,10 @@ template <typename T, typename S> struct StepArgs {
 };
 
 // Counter of the step about to run (0 unless it is needed).
-template <typename S, int MODE, typename Args>
+template <typename S, int MODE, int FL, typename Args>
 __device__ __forceinline__ uint32_t step_key(const Args& a) {
   if constexpr (MODE == kModeStep && Codec<S>::kShifted) {
-    if (a.stochastic) return a.rng[a.rng_idx];
+    if (FL == kFlExpPlain || a.stochastic) return a.rng[a.rng_idx];
   }
   return 0u;
 }
@@ -225,7 +232,7 @@ __device__ __forceinline__ uint64_t step_smem_init(const StepSmem<Q, S, W, NS>& 
 // `rev` the segment is marched upwards (row y0 + Lr + R - 1 first); the node
 // arithmetic is the same in either direction.  Returns false if a stage never
 // arrived (the status word then has kStatusTimeout).
-template <int Q, typename S, int W, int NS, int MODE, typename Args>
+template <int Q, typename S, int W, int NS, int MODE, int FL, typename Args>
 __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensorMap* flg,
                                               const Args& a, int x0, int y0, int Lr, bool rev,
                                               const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
@@ -234,6 +241,8 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
   using L = Lattice<Q>;
   using T = typename Codec<S>::T;
   using C = Codec<S>;
+  static_assert(!C::kShifted, "16-bit storage runs the paired march");
+  constexpr int kPsiKind = FL == kFlExpPlain ? 0 : -1;
   constexpr int R = Sh::R;
   constexpr int GX = Sh::GX;
   constexpr int GY = Sh::GY;
@@ -255,7 +264,6 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
-  const uint32_t key = step_key<S, MODE>(a);
 
   // Every thread is done with the stages and ring of the previous segment.
   __syncthreads();
@@ -294,7 +302,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
   auto load_pop = [&](const S* st, auto ic, int xl) -> T {
     constexpr int i = decltype(ic)::value;
     constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-    return C::dec(st[off + xl], T(a.phys.shift[i]));
+    return C::load(st[off + xl]);
   };
   auto psi_at = [&](const S* st, int xl) -> T {
     T rho = 0;
@@ -302,7 +310,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
       const T v = load_pop(st, ic, xl);
       rho = (decltype(ic)::value == 0) ? v : rho + v;
     });
-    return pseudo_potential<Q, T>(a.phys, rho);
+    return pseudo_potential<Q, T, kPsiKind>(a.phys, rho);
   };
   auto flags_of = [&](const unsigned char* st) -> uint32_t {
     return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::POP_BYTES)[warp] : 0u;
@@ -343,7 +351,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
         if constexpr (Sh::kRegs) fnext[i] = v;
         rho = (i == 0) ? v : rho + v;
       });
-      ring_row[tid + Sh::RO] = pseudo_potential<Q, T>(a.phys, rho);
+      ring_row[tid + Sh::RO] = pseudo_potential<Q, T, kPsiKind>(a.phys, rho);
       if constexpr (Sh::kRegs) flag_next = flags_of(stb);
     }
     // The 2R halo columns by the first 2R threads (one warp diverges, not two).
@@ -422,29 +430,12 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
         if constexpr (MODE == kModeStep) {
           const T usx = ux + div_rho<T>(Fx, rho, inv_rho);
           const T usy = uy + div_rho<T>(Fy, rho, inv_rho);
-          if (a.phys.project) project<Q, T>(f, rho, jx, jy);
+          if (FL != kFlExpPlain && a.phys.project) project<Q, T>(f, rho, jx, jy);
           node_collide<Q, T>(a.phys, f, rho, ux, uy, usx, usy);
-          // Encode once (stochastic rounding draws its bits from the node and
-          // the step), then the primary store plus periodic images inside the
-          // ghost frame.
+          // The primary store plus periodic images inside the ghost frame.
           S e[Q];
-          if constexpr (C::kShifted) {
-            if (a.stochastic) {
-              const uint32_t h = sr_hash((uint32_t)x, (uint32_t)yo, key);
-              static_for<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                e[i] = C::enc_sr(f[i], T(a.phys.shift[i]), h * sr_multiplier(i));
-              });
-            } else {
-              static_for<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                e[i] = C::enc(f[i], T(a.phys.shift[i]));
-              });
-            }
-          } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) e[i] = C::enc(f[i], T(0));
-          }
+          for (int i = 0; i < Q; ++i) e[i] = C::store_rn(f[i]);
           S* out = a.fout + (int64_t)(yo + GY) * a.pitch + x + GX;
           static_for<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
@@ -516,7 +507,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
 // (D2Q21) the collision re-reads them from the row's stage, as march_segment
 // does.  Wall terms, ghost images, the halo psi and a pair that straddles the
 // lattice's right edge fall back to per-node code.
-template <int Q, typename S, int W, int NS, int MODE, typename Args>
+template <int Q, typename S, int W, int NS, int MODE, int FL, typename Args>
 __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUtensorMap* flg,
                                                  const Args& a, int x0, int y0, int Lr, bool rev,
                                                  const StepSmem<Q, S, W, NS>& sm, uint32_t& g) {
@@ -533,6 +524,8 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
   constexpr int P = Sh::V / 2;  // node pairs per thread
   constexpr bool kRegs = Sh::kRegs;
   static_assert(Sh::V % 2 == 0 && RO % 2 == 0 && RO >= R, "paired march");
+  constexpr int kPsiKind = FL == kFlExpPlain ? 0 : -1;
+  constexpr bool kFastExp = C::kShifted;
   unsigned char* const stages = sm.stages;
   uint64_t* const bars = sm.bars;
   T* const ring = sm.ring;
@@ -549,7 +542,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
-  const uint32_t key = step_key<S, MODE>(a);
+  const uint32_t key = step_key<S, MODE, FL>(a);
 
   __syncthreads();
 
@@ -578,28 +571,39 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
     issued = n0;
   }
 
-  // Population I of the columns of pair p: an aligned pair when c_x is even
-  // (one access), else two single loads.
+  // Stored value I of the columns of pair p (f, or the scaled deviation h for
+  // 16-bit storage): an aligned pair when c_x is even (one access), else two
+  // single loads.
   auto load_pair = [&](const S* st, auto ic, int p) -> F2 {
     constexpr int i = decltype(ic)::value;
     constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-    const F2 wrs = F2::splat(a.phys.shift[i]);
     const int xc = xa + 2 * p;
     if constexpr ((off & 1) == 0) {
-      return PR::dec(*reinterpret_cast<const typename PR::Raw*>(st + off + xc), wrs);
+      return PR::load(*reinterpret_cast<const typename PR::Raw*>(st + off + xc));
     } else {
-      return PR::dec1(st[off + xc], st[off + xc + 1], wrs);
+      return PR::load1(st[off + xc], st[off + xc + 1]);
     }
   };
+  // rho from the sum H of a node's stored values: H itself, or for 16-bit
+  // storage H / sigma + rho_s (the shifts w_i rho_s sum to rho_s).
+  constexpr T kInvScale = T(1) / T(C::kScale);
+  auto rho_of = [&](T H) -> T {
+    if constexpr (C::kShifted) return fmaf(H, kInvScale, a.phys.rho_s);
+    else return H;
+  };
+  auto rho_of2 = [&](F2 H) -> F2 {
+    if constexpr (C::kShifted) return fma2(H, F2::splat(kInvScale), F2::splat(a.phys.rho_s));
+    else return H;
+  };
   auto psi_at = [&](const S* st, int xl) -> T {  // one node (halo columns)
-    T rho = 0;
+    T H = 0;
     static_for<0, Q>([&](auto ic) {
       constexpr int i = decltype(ic)::value;
       constexpr int off = Sh::kTab.pop_row[i] + GX - L::cx(i);
-      const T v = C::dec(st[off + xl], a.phys.shift[i]);
-      rho = (i == 0) ? v : rho + v;
+      const T v = C::load(st[off + xl]);
+      H = (i == 0) ? v : H + v;
     });
-    return pseudo_potential<Q, T>(a.phys, rho);
+    return pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho_of(H));
   };
 
   // The thread's columns lie in one 32-column flag chunk.
@@ -608,8 +612,8 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
                    : 0u;
   };
 
-  // kRegs: populations and rho (summed once, in table order) of the row whose
-  // psi was just formed, collided in the next iteration.
+  // kRegs: stored values and their sum H (formed once, in table order) of the
+  // row whose psi was just formed, collided in the next iteration.
   F2 fnext[kRegs ? P : 1][kRegs ? Q : 1];
   F2 rho_next[P];
   uint32_t flag_next = 0;
@@ -644,17 +648,18 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
     T* ring_row = ring + (k % Sh::RING_H) * Sh::RING_W;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      F2 rho;
+      F2 H;
       static_for<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const F2 v = load_pair(st, ic, p);
         if constexpr (kRegs) fnext[p][i] = v;
-        rho = (i == 0) ? v : rho + v;
+        H = (i == 0) ? v : H + v;
       });
-      const T pa = pseudo_potential<Q, T>(a.phys, rho.x());
-      const T pb = pseudo_potential<Q, T>(a.phys, rho.y());
+      const F2 rho = rho_of2(H);
+      const T pa = pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.x());
+      const T pb = pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.y());
       *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = make_float2(pa, pb);
-      if constexpr (kRegs) rho_next[p] = rho;
+      if constexpr (kRegs) rho_next[p] = H;
     }
     if constexpr (kRegs) flag_next = flags_of(stb);
     if (tid < 2 * R) {
@@ -693,24 +698,32 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
       for (int p = 0; p < P; ++p) {
         const int xp = x + 2 * p;           // first column of pair p
         const bool pair_ok = xp + 1 < a.nx;  // both nodes exist
+        // f_: the stored values (f, or h = sigma (f - w rho_s) for 16-bit
+        // storage).  H: their sum in table order (the psi pass's sum), rho
+        // from it; J = sum f_i c_i (D2Q9: the diagonal differences f5 - f7
+        // and f8 - f6 shared by its two components; otherwise in table
+        // order), j = J / sigma (the shifts carry no momentum).
         F2 (&f_)[Q] = f[p];
-        // rho of both nodes in table order (the psi pass's sum); j (D2Q9:
-        // the diagonal differences f5 - f7 and f8 - f6 shared by its two
-        // components; otherwise in table order).
-        const F2 rho = rho_cur[p];
-        F2 jx, jy;
+        const F2 Hm = rho_cur[p];
+        const F2 rho = rho_of2(Hm);
+        F2 Jx, Jy;
         if constexpr (Q == 9) {
           const F2 d57 = f_[5] - f_[7], d86 = f_[8] - f_[6];
-          jx = ((f_[1] - f_[3]) + d57) + d86;
-          jy = ((f_[2] - f_[4]) + d57) - d86;
+          Jx = ((f_[1] - f_[3]) + d57) + d86;
+          Jy = ((f_[2] - f_[4]) + d57) - d86;
         } else {
-          jx = F2::splat(0.f);
-          jy = F2::splat(0.f);
+          Jx = F2::splat(0.f);
+          Jy = F2::splat(0.f);
           static_for<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            if constexpr (L::cx(i) != 0) jx = fma2(f_[i], F2::splat(T(L::cx(i))), jx);
-            if constexpr (L::cy(i) != 0) jy = fma2(f_[i], F2::splat(T(L::cy(i))), jy);
+            if constexpr (L::cx(i) != 0) Jx = fma2(f_[i], F2::splat(T(L::cx(i))), Jx);
+            if constexpr (L::cy(i) != 0) Jy = fma2(f_[i], F2::splat(T(L::cy(i))), Jy);
           });
+        }
+        F2 jx = Jx, jy = Jy;
+        if constexpr (C::kShifted && C::kScale != 1.0f) {
+          jx = Jx * F2::splat(kInvScale);
+          jy = Jy * F2::splat(kInvScale);
         }
         const F2 inv_rho(rcp_node<S, float>(rho.x()), rcp_node<S, float>(rho.y()));
         const F2 ux = jx * inv_rho;
@@ -807,63 +820,88 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
             const F2 us2 = fma2(usy, usy, usx * usx), u2 = fma2(uy, uy, ux * ux);
             const F2 wB = fma2(fma2(ngg, u2, us2), F2::splat(-T(E::inv_2theta)),
                                F2::splat(a.phys.omega));
-            if (a.phys.project) {
-              // rare path: per node
+            if (FL != kFlExpPlain && a.phys.project) {
+              // rare path: per node.  The projection is linear and maps the
+              // shift w_i rho_s to itself, so it acts on h with (H, J) as it
+              // acts on f with (rho, j).
               T fa[Q], fb[Q];
   #pragma unroll
               for (int i = 0; i < Q; ++i) {
                 fa[i] = f_[i].x();
                 fb[i] = f_[i].y();
               }
-              project<Q, T>(fa, rho.x(), jx.x(), jy.x());
-              project<Q, T>(fb, rho.y(), jx.y(), jy.y());
+              project<Q, T>(fa, Hm.x(), Jx.x(), Jy.x());
+              project<Q, T>(fb, Hm.y(), Jx.y(), Jy.y());
   #pragma unroll
               for (int i = 0; i < Q; ++i) f_[i] = F2(fa[i], fb[i]);
             }
-            static_for<0, Q>([&](auto ic) {
-              constexpr int i = decltype(ic)::value;
-              constexpr int j = opposite<Q>(i);
-              // The rest population comes from the mass closure below.
-              if constexpr (i != L::REST && i < j) {
-                const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
-                const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
-                const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax3, ay3);
-                const F2 wr = F2::splat(T(L::w(i))) * rho;
-                const F2 t = fma2(ngg, cu * cu, cs * cs);
-                const F2 sb = fma2(t, F2::splat(T(E::inv_2theta2)), wB);
-                const F2 fi = fma2(gg, f_[i], wr * (sb + ca));
-                const F2 fj = fma2(gg, f_[j], wr * (sb - ca));
-                f_[i] = fi;
-                f_[j] = fj;
-              }
-            });
-            {  // mass closure of the rest population (FP32 arithmetic)
+            if constexpr (C::kShifted) {
+              // The same update on h = sigma (f - w rho_s):
+              //   h_post(+-c) = g h(+-c) + sigma w [rho (sb +- ca) - omega rho_s].
+              const F2 nwr = F2::splat(a.phys.neg_omega_rho_s);
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int j = opposite<Q>(i);
+                if constexpr (i != L::REST && i < j) {
+                  const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
+                  const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
+                  const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax3, ay3);
+                  const F2 t = fma2(ngg, cu * cu, cs * cs);
+                  const F2 sb = fma2(t, F2::splat(T(E::inv_2theta2)), wB);
+                  const F2 z = fma2(rho, sb, nwr);
+                  const F2 sw = F2::splat(T(C::kScale * L::w(i)));
+                  const F2 hi = fma2(gg, f_[i], sw * fma2(rho, ca, z));
+                  const F2 hj = fma2(gg, f_[j], sw * fma2(rho, -ca, z));
+                  f_[i] = hi;
+                  f_[j] = hj;
+                }
+              });
+            } else {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int j = opposite<Q>(i);
+                // The rest population comes from the mass closure below.
+                if constexpr (i != L::REST && i < j) {
+                  const F2 cs = cdot2<L::cx(i), L::cy(i)>(usx, usy);
+                  const F2 cu = cdot2<L::cx(i), L::cy(i)>(ux, uy);
+                  const F2 ca = cdot2<L::cx(i), L::cy(i)>(ax3, ay3);
+                  const F2 wr = F2::splat(T(L::w(i))) * rho;
+                  const F2 t = fma2(ngg, cu * cu, cs * cs);
+                  const F2 sb = fma2(t, F2::splat(T(E::inv_2theta2)), wB);
+                  const F2 fi = fma2(gg, f_[i], wr * (sb + ca));
+                  const F2 fj = fma2(gg, f_[j], wr * (sb - ca));
+                  f_[i] = fi;
+                  f_[j] = fj;
+                }
+              });
+            }
+            {  // mass closure of the rest population: the stored values sum to
+               // H (rho, or sigma (rho - rho_s) for 16-bit storage) after the
+               // collision as before it
               constexpr int i0 = L::REST == 0 ? 1 : 0;
               F2 moving = f_[i0];
 #pragma unroll
               for (int i = i0 + 1; i < Q; ++i)
                 if (i != L::REST) moving += f_[i];
-              f_[L::REST] = rho - moving;
+              f_[L::REST] = Hm - moving;
             }
-            // Encode both nodes once (stochastic rounding: bits from the node pair
-            // and the step), then the primary store plus periodic images.
+            // Round both nodes once (stochastic rounding: bits from the node
+            // pair and the step), then the primary store plus periodic images.
             typename PR::Raw raw[Q];
             if constexpr (C::kShifted) {
-              if (a.stochastic) {
+              if (FL == kFlExpPlain || a.stochastic) {
                 const uint32_t h = sr_hash((uint32_t)xp, (uint32_t)yo, key);
                 static_for<0, Q>([&](auto ic) {
                   constexpr int i = decltype(ic)::value;
-                  raw[i] = PR::enc_sr(f_[i], F2::splat(a.phys.enc_add[i]), h * sr_multiplier(i));
+                  raw[i] = PR::store_sr(f_[i], h * sr_multiplier(i));
                 });
               } else {
-                static_for<0, Q>([&](auto ic) {
-                  constexpr int i = decltype(ic)::value;
-                  raw[i] = PR::enc(f_[i], F2::splat(a.phys.enc_add[i]));
-                });
+  #pragma unroll
+                for (int i = 0; i < Q; ++i) raw[i] = PR::store_rn(f_[i]);
               }
             } else {
   #pragma unroll
-              for (int i = 0; i < Q; ++i) raw[i] = PR::enc(f_[i], F2::splat(0.f));
+              for (int i = 0; i < Q; ++i) raw[i] = PR::store_rn(f_[i]);
             }
             S* out = a.fout + (int64_t)(yo + GY) * a.pitch + xp + GX;
             if (pair_ok) {
@@ -944,15 +982,15 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
 
 // Marches one segment with the variant the shape selects (one or two nodes
 // per thread).
-template <int Q, typename S, int W, int NS, int MODE, typename Args>
+template <int Q, typename S, int W, int NS, int MODE, int FL, typename Args>
 __device__ __forceinline__ bool march_any(const PopMaps* src, const CUtensorMap* flg,
                                           const Args& a, int x0, int y0, int Lr, bool rev,
                                           const StepSmem<Q, S, W, NS>& sm, uint32_t& g,
                                           uint64_t policy) {
   if constexpr (StepShape<Q, S, W, NS>::V >= 2)
-    return march_segment_v2<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g);
+    return march_segment_v2<Q, S, W, NS, MODE, FL>(src, flg, a, x0, y0, Lr, rev, sm, g);
   else
-    return march_segment<Q, S, W, NS, MODE>(src, flg, a, x0, y0, Lr, rev, sm, g, policy);
+    return march_segment<Q, S, W, NS, MODE, FL>(src, flg, a, x0, y0, Lr, rev, sm, g, policy);
 }
 
 // One time step of one lattice: CTA (bx, by) marches strip bx, segment by.
@@ -960,7 +998,7 @@ __device__ __forceinline__ bool march_any(const PopMaps* src, const CUtensorMap*
 // at about the same time, pull the rows they share (the 2R halo rows of their
 // common edge) both at their start or both at their end: the second pull of
 // such a row is an L2 hit instead of a DRAM read.
-template <int Q, typename S, int W, int NS, int MODE, int MINB>
+template <int Q, typename S, int W, int NS, int MODE, int MINB, int FL>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     step_kernel(const __grid_constant__ PopMaps src, const __grid_constant__ CUtensorMap flg,
                 const StepArgs<typename Codec<S>::T, S> a) {
@@ -978,7 +1016,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   // Every CTA reads the counter in march_any before this launch ends; the
   // word written here is read only by the next step.
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) advance_key<MODE>(a);
-  march_any<Q, S, W, NS, MODE>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
+  march_any<Q, S, W, NS, MODE, FL>(&src, &flg, a, blockIdx.x * W, y0, min(a.tile_rows, a.ny - y0),
                                (blockIdx.y & 1u) != 0u, sm, g, policy);
 }
 
@@ -1026,7 +1064,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     const auto& a = P.a[tile.member][dir];
     if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(a);
     const auto* m = &members[tile.member];
-    return march_any<Q, S, W, NS, kModeStep>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
+    return march_any<Q, S, W, NS, kModeStep, kFlRuntime>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
                                             tile.rows, tile.rev != 0, sm, g, policy);
   };
   if constexpr (PERSIST) {

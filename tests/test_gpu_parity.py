@@ -6,8 +6,6 @@ and 1e-5 absolute in u (lattice units).  Wherever the oracle can run the same
 inputs, the comparison is element by element.  At the 8192x4096 size the
 oracle recomputes sampled nodes one by one from a periodic window around each.
 """
-import math
-
 import numpy as np
 import pytest
 
@@ -343,12 +341,6 @@ def test_full_size_fp32_sampled_nodes_match_oracle(pkg):
         assert err < 1e-5, (y, x, err)
 
 
-def _shift12(x):
-    """w_i shift_rho rounded to 12 significant bits (the storage shift lbm.h defines)."""
-    m, e = math.frexp(x)
-    return math.ldexp(round(math.ldexp(x, 12 - e)), e - 12)
-
-
 def _ulp16(v, storage):
     """Unit in the last place of the 16-bit number holding v: binary16 (FP16S
     stores the deviation scaled by 2^8, normal from 2^-14, subnormal step 2^-24)
@@ -374,7 +366,7 @@ def test_full_size_16bit_sampled_nodes_match_oracle(pkg, storage):
     sim.step(1)
     f1 = sim.populations()
     p, r = oracle_params(w), 4
-    shift = np.array([_shift12(wi * 1.0) for wi in O.LATTICES[9].w])
+    shift = O.LATTICES[9].w * 1.0          # w_i rho_s, rho_s = 1
     scale = 256.0 if storage == "fp16s" else 1.0
     rng = np.random.default_rng(1)
     lay = sim.layout()
@@ -409,7 +401,7 @@ def test_d2q21_16bit_sampled_nodes_match_oracle(pkg, storage):
     sim.step(1)
     f1 = sim.populations()
     p, r = oracle_params(w), 7
-    shift = np.array([_shift12(wi * 1.0) for wi in O.LATTICES[21].w])
+    shift = O.LATTICES[21].w * 1.0
     scale = 256.0 if storage == "fp16s" else 1.0
     rng = np.random.default_rng(2)
     lay = sim.layout()
