@@ -66,10 +66,14 @@ enum {
 
 enum { LBM_D2Q9 = 9, LBM_D2Q21 = 21 };
 
-/* Population storage.  FP16S / BF16S store the deviation f_i - shift_i in 16
- * bits, shift_i = w_i * shift_rho rounded to 12 significant bits (FP16S scaled
- * by 2^8: |f_i - shift_i| < 256, beyond which the stored value becomes inf and
- * the non-finite check reports it); all arithmetic is FP32.  The step rounds
+/* Population storage.  FP16S / BF16S store the deviation from the shift
+ * w_i rho_s in 16 bits, h_i = sigma (f_i - w_i rho_s), where rho_s is
+ * shift_rho rounded to FP32 and sigma = 2^8 for FP16S (|f_i - w_i rho_s| < 256,
+ * beyond which the stored value becomes inf and the non-finite check reports
+ * it) and 1 for BF16S.  All arithmetic of the step is FP32 and works on h
+ * directly (rho = sum_i h_i / sigma + rho_s, j = sum_i h_i c_i / sigma; the
+ * collision maps deviations to deviations); set-up and read-out convert
+ * between f and h in FP64.  The step rounds
  * the stored deviations stochastically by default (LBM_ROUND_STOCHASTIC: the
  * expectation of the stored value is the FP32 value; the random bits are a
  * counter-based hash of the node and the step, so runs are reproducible and a
@@ -276,7 +280,14 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * at most 2^28 elements (4096 blocks of 65536), and larger n returns LBM_EINVAL
  * with the limit in lbm_last_error(NULL).  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) once, with the device
- * current; make that first call before any stream capture.  Work is enqueued
+ * current; with CUDA's default lazy module loading that first call is also
+ * when the array and these kernels are loaded onto the device, which takes
+ * device memory.  So make the first call on every device during start-up
+ * (a call with n = 0 does it and writes zeros), before any stream capture and
+ * before the point after which the caller may not allocate.  The cached
+ * address belongs to the device's primary context: after that context is
+ * reset (cudaDeviceReset or a primary-context reset by any component of the
+ * process) this entry point must not be called again.  Work is enqueued
  * on cuda_stream (NULL = legacy default stream) and the call returns without
  * synchronising.  Every call on a device shares the one array, so calls whose
  * kernels overlap on the GPU (different streams, no ordering between them)

@@ -57,3 +57,25 @@ def test_noalloc_reduction_rejects_sizes_beyond_its_scratch():
                                  None)
     assert rc == _lib.LBM_EINVAL
     assert b"scratch limit" in lib.lbm_last_error(None)
+
+
+def test_noalloc_reduction_null_arrays_and_empty_input():
+    """A NULL array sums to zero and n = 0 writes zeros (the start-up call
+    that loads the scratch array on a device)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1202_6130_gb300 import _lib
+    lib = _lib.load()
+    a = torch.linspace(0.5, 2.0, 70001, dtype=torch.float64, device="cuda")
+    out = torch.full((3,), 7.0, dtype=torch.float64, device="cuda")
+    rc = lib.lbm_reduce3_noalloc(ctypes.c_void_p(a.data_ptr()), None, None, a.numel(),
+                                 ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 0, lib.lbm_last_error(None)
+    got = out.cpu().numpy()
+    want = float(a.sum().item())
+    assert abs(got[0] - want) <= 1e-13 * abs(want) and got[1] == 0.0 and got[2] == 0.0
+    out.fill_(7.0)
+    rc = lib.lbm_reduce3_noalloc(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                 None, 0, ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 0, lib.lbm_last_error(None)
+    assert out.cpu().numpy().tolist() == [0.0, 0.0, 0.0]
