@@ -244,3 +244,38 @@ def drop_velocity(rho: np.ndarray, ux: np.ndarray, rho_mid: float, phi_s=None) -
     if phi_s is not None:
         m &= phi_s < 0.5
     return float((rho[m] * ux[m]).sum() / rho[m].sum())
+
+
+def contact_angles_of_drops(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
+                            y_max: int | None = None, min_width: int = 12):
+    """Static angles of every drop resting on the bottom wall of a periodic
+    lattice holding many of them: the liquid above the solid surface (rho
+    above the mid density, phi_S < 0.5, below ``y_max``) is split into
+    connected pieces (periodic in x), and each piece at least ``min_width``
+    columns wide gets the circle fit of ``contact_angle`` over its own columns.
+    Returns a list of (x_centre, theta_deg, R), sorted by x_centre."""
+    from scipy import ndimage
+    ny, nx = rho.shape
+    y_max = ny // 2 if y_max is None else y_max
+    mid = 0.5 * (rho_l + rho_v)
+    liquid = (rho > mid) & (phi_s < 0.5)
+    liquid[y_max:, :] = False
+    cols = liquid.any(axis=0)
+    if cols.all():
+        raise ValueError("liquid spans every column: no drop boundary")
+    shift = -int(np.argmin(cols))          # roll a dry column to x = 0
+    rho_r = np.roll(rho, shift, axis=1)
+    phi_r = np.roll(phi_s, shift, axis=1)
+    lab, n = ndimage.label(np.roll(liquid, shift, axis=1))
+    out = []
+    for sl in ndimage.find_objects(lab):
+        x0, x1 = sl[1].start, sl[1].stop
+        if x1 - x0 < min_width:
+            continue
+        try:
+            c = contact_angle(rho_r, phi_r, rho_l, rho_v, x_range=(max(0, x0 - 2), min(nx, x1 + 2)),
+                              y_max=y_max)
+        except ValueError:
+            continue
+        out.append((float((c.xc - shift) % nx), c.theta_deg, c.R))
+    return sorted(out)

@@ -36,6 +36,7 @@ struct lbm_ctx {
   void* wall_uwy = nullptr;
   uint32_t* wall_flags = nullptr;  // [ny][nchunk_pad]
   int nchunk_pad = 0;
+  int flag_box = 0;                // flag words per TMA box (ConfigShape::FLAG_BOX)
   CUtensorMap flag_map;
   bool has_wall = false;
   uint32_t* d_status = nullptr;  // 256 bytes: word 0 status bits, words kRngWord.. step counter
@@ -196,13 +197,14 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
 // active tiles in a compact band of rows and balance the SMs dynamically; with
 // adjacent segments marching in opposite directions the 2R halo rows they
 // share are pulled at about the same time and the second pull hits in L2.
-// FP32 is fastest at 12 rows, 16-bit storage near 24, FP64 near 64.  Small
+// FP32 is fastest at 4-6 rows (0.367-0.370 ms against 0.385 ms at 12), 16-bit
+// storage near 24, FP64 near 64.  Small
 // lattices get shorter segments so that the grid still covers at least two
 // waves of resident CTAs.
 int choose_tile_rows(int nx, int ny, int W, int esize, int R, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  int L = esize == 2 ? 24 : (esize == 4 ? 12 : 64);
+  int L = esize == 2 ? 24 : (esize == 4 ? 6 : 64);
   if (R > 1) L = std::max(L, 16 * R);
   while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
   return std::max(1, std::min(L, ny));
@@ -216,6 +218,7 @@ template <int Q, typename S> int setup_layout(lbm_ctx* c) {
   c->GY = Sh::GY;
   c->esize = (int)sizeof(S);
   c->W = StepConfig<Q, S>::W;
+  c->flag_box = Sh::FLAG_BOX;
   c->NS = StepConfig<Q, S>::NS;
   c->pitch = ((int64_t)(c->p.nx + 2 * Sh::GX) + 31) / 32 * 32;
   c->rows = c->p.ny + 2 * Sh::GY;
@@ -251,6 +254,7 @@ template <typename T> Physics<T> make_physics(const lbm_ctx* c) {
   P.G = (T)p.G;
   P.rho0 = (T)p.rho0;
   P.inv_rho0 = (T)(1.0 / p.rho0);
+  P.exp2_scale = (T)(-1.4426950408889634 / p.rho0);  // -log2(e) / rho0
   P.eos_tv = (T)p.eos_theta_v;
   P.eos_tu = (T)p.eos_theta_u;
   P.eos_tl = (T)p.eos_theta_l;
@@ -451,7 +455,7 @@ int lbm_set_wall(lbm_ctx* c, const double* phi_s, const double* psi_r, const dou
     if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)c->nchunk_pad, (cuuint64_t)ny};
     cuuint64_t strides[1] = {(cuuint64_t)c->nchunk_pad * 4};
-    cuuint32_t box[2] = {(cuuint32_t)(c->W / 32), 1};
+    cuuint32_t box[2] = {(cuuint32_t)c->flag_box, 1};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&c->flag_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, c->wall_flags, dims, strides,
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -818,6 +822,7 @@ struct lbm_batch {
     std::vector<unsigned char> args;  // host copy of BatchArgs<T, S>
     int base = 0, count = 0;          // members [base, base + count)
     int tile_off = 0, first_off = 0, nctas = 0;
+    bool plain = false;               // every member: exponential psi, no projection, SR
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
   };
@@ -931,8 +936,11 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     ch.count = std::min(kBatchChunk, n - ch.base);
     ch.args.assign(sizeof(A), 0);
     A* pa = reinterpret_cast<A*>(ch.args.data());
+    ch.plain = true;
     for (int i = 0; i < ch.count; ++i) {
       lbm_ctx* c = b->members[ch.base + i];
+      ch.plain = ch.plain && c->p.psi_kind == LBM_PSI_EXP && !c->p.project &&
+                 (!Codec<S>::kShifted || c->p.rounding == LBM_ROUND_STOCHASTIC);
       for (int d = 0; d < 2; ++d)
         pa->a[i][d] = make_args<Q, S>(c, d, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
       pa->cur[i] = c->cur;
@@ -1007,7 +1015,7 @@ template <int Q, typename S> cudaError_t batch_launch(lbm_batch* b, int parity) 
         static_cast<const BatchMember<T, S>*>(b->d_members) + ch.base,
         static_cast<const BatchTile*>(b->d_tiles) + ch.tile_off,
         static_cast<const int32_t*>(b->d_first) + ch.first_off, ch.nctas, parity, b->ctas > 0,
-        multi ? ch.stream : b->stream);
+        ch.plain, multi ? ch.stream : b->stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -20,7 +20,7 @@ namespace lbm {
 // its plane groups arrive as boxes of depth 1, 3 and 7 (37 KB per CTA).)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
-  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 6)) : 5;
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 5)) : 5;
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
                                        : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 6));
   // The batch kernel carries its tile loop on top of the march: 16-bit D2Q9
@@ -41,12 +41,14 @@ cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
 template <int Q, typename S> int step_ctas_per_sm();
 
 // One time step of up to kBatchChunk members of a batch (CTA b marches tiles
-// [first[b], first[b + 1])), and its residency per SM.
+// [first[b], first[b + 1])), and its residency per SM.  `plain`: every member
+// has the exponential psi, no projection and (16-bit storage) stochastic
+// rounding, so the kernel with those settings fixed runs.
 template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
                          const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         bool persistent, cudaStream_t stream);
+                         bool persistent, bool plain, cudaStream_t stream);
 template <int Q, typename S> int batch_ctas_per_sm();
 
 // Auxiliary kernels (aux.cu).

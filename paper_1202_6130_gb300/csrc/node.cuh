@@ -164,6 +164,7 @@ template <typename T> struct Physics {
   T G;               // fluid-fluid coupling in F_FF = -G psi sum w psi r
   T rho0;            // exponential psi scale
   T inv_rho0;        // 1 / rho0
+  T exp2_scale;      // -log2(e) / rho0: exp(-rho / rho0) = 2^(rho exp2_scale)
   T eos_tv, eos_tu, eos_tl, eos_r1, eos_r2, eos_p1, eos_p2;
   T bfx, bfy;        // body-force density
   T rho_s;           // FP16S / BF16S shift density (stored h_i = sigma (f_i - w_i rho_s))
@@ -218,19 +219,36 @@ template <typename T> __device__ __forceinline__ T t_sqrt(T v);
 template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
 template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
 
+// 2^x by the hardware base-2 exponential (PTX ex2.approx.ftz.f32: a few
+// units in the last place over the range used here).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Exponential psi with FAST arithmetic: rho0 (1 - exp(-rho / rho0)) as
+// rho0 - rho0 2^(rho c), c = -log2(e) / rho0, from the identity
+// exp(y) = 2^(y log2 e).  One product, one hardware exponential and one fused
+// multiply-add; about 2e-7 relative for the densities of a liquid-vapour
+// system.  Used with 16-bit storage, whose rounding is about 2^-11 of a
+// stored deviation; FP32 and FP64 storage keep expf / exp.
+__device__ __forceinline__ float psi_exp_fast(float rho, float exp2_scale, float rho0) {
+  return fmaf(ex2_approx(rho * exp2_scale), -rho0, rho0);
+}
+
 // psi(rho): exponential (Shan-Chen) or sqrt(2 [rho theta - p_EOS(rho)]) with the
 // piecewise-linear Eq. EOS.  KIND: the kind if known at compile time (0
-// exponential, 1 EOS), else -1 (P.psi_kind decides).  FAST: the exponential
-// by the hardware base-2 exponential (__expf: a few ulp, where expf is within
-// one); used with 16-bit storage, whose rounding is about 2^-11 of a deviation.
+// exponential, 1 EOS), else -1 (P.psi_kind decides).  FAST: psi_exp_fast for
+// the exponential kind (FP32 arithmetic).
 template <int Q, typename T, int KIND = -1, bool FAST = false>
 __device__ __forceinline__ T pseudo_potential(const Physics<T>& P, T rho) {
   if (KIND == 0 || (KIND < 0 && P.psi_kind == 0)) {
+    if constexpr (FAST && sizeof(T) == 4) return psi_exp_fast(rho, P.exp2_scale, P.rho0);
     // FP64 divides like the oracle; FP32 multiplies by the reciprocal (exact
     // for the usual rho0 = 1).
     const T arg = sizeof(T) == 8 ? -rho / P.rho0 : -rho * P.inv_rho0;
-    if constexpr (FAST && sizeof(T) == 4) return P.rho0 * (T(1) - __expf(arg));
-    else return P.rho0 * (T(1) - t_exp<T>(arg));
+    return P.rho0 * (T(1) - t_exp<T>(arg));
   }
   constexpr T theta = T(Lattice<Q>::THETA);
   T p;

@@ -76,46 +76,61 @@ template <int Q, typename S> int step_ctas_per_sm() {
   return n;
 }
 
-template <int Q, typename S>
+template <int Q, typename S, int FL>
 static cudaError_t prepare_batch_kernel() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   static cudaError_t once = [] {
-    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(
+        batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>,
+    return cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   }();
   return once;
+}
+
+template <int Q, typename S, int FL>
+static cudaError_t launch_batch_fl(const BatchArgs<typename Codec<S>::T, S>& args,
+                                   const BatchMember<typename Codec<S>::T, S>* members,
+                                   const BatchTile* tiles, const int32_t* first, int nctas,
+                                   int parity, bool persistent, cudaStream_t stream) {
+  using Cfg = StepConfig<Q, S>;
+  using Sh = ConfigShape<Q, S>;
+  cudaError_t e = prepare_batch_kernel<Q, S, FL>();
+  if (e != cudaSuccess) return e;
+  if (persistent)
+    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>
+        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
+  else
+    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>
+        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
+  return cudaGetLastError();
 }
 
 template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
                          const BatchMember<typename Codec<S>::T, S>* members,
                          const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         bool persistent, cudaStream_t stream) {
-  using Cfg = StepConfig<Q, S>;
-  using Sh = ConfigShape<Q, S>;
-  cudaError_t e = prepare_batch_kernel<Q, S>();
-  if (e != cudaSuccess) return e;
-  if (persistent)
-    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>
-        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
-  else
-    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false>
-        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
-  return cudaGetLastError();
+                         bool persistent, bool plain, cudaStream_t stream) {
+  return plain ? launch_batch_fl<Q, S, kFlExpPlain>(args, members, tiles, first, nctas, parity,
+                                                    persistent, stream)
+               : launch_batch_fl<Q, S, kFlRuntime>(args, members, tiles, first, nctas, parity,
+                                                   persistent, stream);
 }
 
+// Residency per SM of the persistent batch kernel; also sets the shared-memory
+// attribute of every batch kernel variant (outside any stream capture).
 template <int Q, typename S> int batch_ctas_per_sm() {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
-  if (prepare_batch_kernel<Q, S>() != cudaSuccess) return 0;
+  if (prepare_batch_kernel<Q, S, kFlRuntime>() != cudaSuccess) return 0;
+  if (prepare_batch_kernel<Q, S, kFlExpPlain>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true>, Sh::NT, Sh::SMEM) !=
-      cudaSuccess)
+          &n, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, kFlRuntime>, Sh::NT,
+          Sh::SMEM) != cudaSuccess)
     return 0;
   return n;
 }
@@ -130,5 +145,5 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   template cudaError_t lbm::launch_batch<Q, S>(                                          \
       const lbm::BatchArgs<lbm::Codec<S>::T, S>&,                                         \
       const lbm::BatchMember<lbm::Codec<S>::T, S>*, const lbm::BatchTile*, const int32_t*, \
-      int, int, bool, cudaStream_t);                                                     \
+      int, int, bool, bool, cudaStream_t);                                               \
   template int lbm::batch_ctas_per_sm<Q, S>();

@@ -111,7 +111,16 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   // 128-byte aligned slot of the stage.
   static constexpr int NBOX = 2 * R + 1;
   static constexpr int CHUNKS = W / 32;  // wall-flag words per row
-  static constexpr int FLAG_SLOT = ((CHUNKS * 4 + 127) / 128) * 128;
+  // The flag words of a strip row arrive as one TMA box of FLAG_BOX words
+  // that starts at a multiple of 4 words (16 bytes) at or below the strip's
+  // first word; FLAG_BOX covers the strip from any such start.
+  static constexpr int flag_box() {
+    int need = CHUNKS;
+    for (int j = 0; j < 4; ++j) need = (CHUNKS * j) % 4 + CHUNKS > need ? (CHUNKS * j) % 4 + CHUNKS : need;
+    return (need + 3) / 4 * 4;
+  }
+  static constexpr int FLAG_BOX = flag_box();
+  static constexpr int FLAG_SLOT = ((FLAG_BOX * 4 + 127) / 128) * 128;
   // Nodes per thread: with FP32 arithmetic (D2Q9; D2Q21 with 16-bit
   // storage) adjacent columns are updated in packed FP32 pairs, one pair per
   // thread; otherwise one node.  (The paired march takes any number of pairs
@@ -124,7 +133,7 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int RING_W = W + 2 * RO;
   static constexpr int RING_H = 2 * R + 2;
   static constexpr uint32_t TX_POP = Q * BW * (uint32_t)sizeof(S);
-  static constexpr uint32_t TX_FLAGS = CHUNKS * 4;
+  static constexpr uint32_t TX_FLAGS = FLAG_BOX * 4;
   // Populations of the node row being collided stay in registers (R = 1) or
   // are re-read from its stage (R > 1, where R rows of Q values would not fit).
   static constexpr bool kRegs = (R == 1);
@@ -176,7 +185,7 @@ template <int Q, typename S, int W, int NS> struct StepShape {
   static constexpr int STAGE = POP_BYTES + FLAG_SLOT;
   static constexpr int SMEM = 128 /*alignment slack*/ + NS * STAGE + NS * 8 +
                               RING_H * RING_W * (int)sizeof(T) + 16;
-  static_assert(W % 32 == 0 && W >= 64 && CHUNKS <= 256, "strip width");
+  static_assert(W % 32 == 0 && W >= 64 && FLAG_BOX <= 256, "strip width");
   static_assert(NT % 32 == 0 && NT >= 32, "threads per CTA");
   static_assert(NS >= R + 2, "pipeline depth");
   static_assert(NMAP <= kMaxMaps && BW <= 256, "tensor-map boxes");
@@ -285,7 +294,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
       constexpr int plane = Sh::kTab.box_plane[j];
       tma_load_3d(st + off, &src->m[map], &bars[s], x0, ynode - cy + GY, plane);
     });
-    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], x0 >> 5, ynode);
+    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], (x0 >> 5) & ~3, ynode);
   };
   int issued = 0;
   if (tid == kIss) {
@@ -296,6 +305,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
     for (int k = 0; k < n0; ++k) issue(k);
     issued = n0;
   }
+  const int flag0 = (x0 >> 5) & 3;  // the strip's first word in the flag box
 
   // Population I of node column xl (relative to x0) from a stage: pulled from
   // column xl - c_x of its box row, whose first element is node column -GX.
@@ -313,7 +323,7 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
     return pseudo_potential<Q, T, kPsiKind>(a.phys, rho);
   };
   auto flags_of = [&](const unsigned char* st) -> uint32_t {
-    return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::POP_BYTES)[warp] : 0u;
+    return wall_on ? reinterpret_cast<const uint32_t*>(st + Sh::POP_BYTES)[flag0 + warp] : 0u;
   };
 
   T fnext[Q];            // kRegs: populations of the row whose psi was just formed
@@ -484,12 +494,15 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
 
   g = g0 + (uint32_t)K;
   if (*s_abort) {
-    // A stage never completed.  Record it, then give the copies still in
-    // flight a bounded chance to land before the shared memory is reused.
+    // A stage never completed.  Record it, then wait (bounded) for the
+    // copies still in flight before the shared memory is reused.  Bytes a
+    // stage was told to expect beyond its copies (the test hook) are retired
+    // first, so each wait ends exactly when its real copies have landed.
     if (tid == kIss) {
       atomicOr(a.status, kStatusTimeout);
       for (int r = k; r < issued; ++r) {
         const uint32_t gr = g0 + (uint32_t)r;
+        if (a.extra_tx) mbar_complete_tx(&bars[gr % NS], a.extra_tx);
         mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u, a.wait_ns);
       }
     }
@@ -559,7 +572,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
       constexpr int plane = Sh::kTab.box_plane[j];
       tma_load_3d(st + off, &src->m[map], &bars[s], x0, ynode - cy + GY, plane);
     });
-    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], x0 >> 5, ynode);
+    if (wall_on) tma_load_2d(st + Sh::POP_BYTES, flg, &bars[s], (x0 >> 5) & ~3, ynode);
   };
   int issued = 0;
   if (tid == kIss) {
@@ -570,6 +583,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
     for (int k = 0; k < n0; ++k) issue(k);
     issued = n0;
   }
+  const int flag0 = (x0 >> 5) & 3;  // the strip's first word in the flag box
 
   // Stored value I of the columns of pair p (f, or the scaled deviation h for
   // 16-bit storage): an aligned pair when c_x is even (one access), else two
@@ -608,7 +622,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
 
   // The thread's columns lie in one 32-column flag chunk.
   auto flags_of = [&](const unsigned char* stage) -> uint32_t {
-    return wall_on ? reinterpret_cast<const uint32_t*>(stage + Sh::POP_BYTES)[xa >> 5]
+    return wall_on ? reinterpret_cast<const uint32_t*>(stage + Sh::POP_BYTES)[flag0 + (xa >> 5)]
                    : 0u;
   };
 
@@ -616,6 +630,7 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
   // row whose psi was just formed, collided in the next iteration.
   F2 fnext[kRegs ? P : 1][kRegs ? Q : 1];
   F2 rho_next[P];
+  F2 nonfinite = F2::splat(0.f);
   uint32_t flag_next = 0;
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
@@ -656,9 +671,18 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
         H = (i == 0) ? v : H + v;
       });
       const F2 rho = rho_of2(H);
-      const T pa = pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.x());
-      const T pb = pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.y());
-      *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = make_float2(pa, pb);
+      float2 psi2;
+      if constexpr (kPsiKind == 0 && kFastExp) {
+        // psi_exp_fast of both nodes, the product and the fused
+        // multiply-add packed
+        const F2 e2 = rho * F2::splat(a.phys.exp2_scale);
+        psi2 = fma2(F2(ex2_approx(e2.x()), ex2_approx(e2.y())), F2::splat(-a.phys.rho0),
+                    F2::splat(a.phys.rho0)).v;
+      } else {
+        psi2 = make_float2(pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.x()),
+                           pseudo_potential<Q, T, kPsiKind, kFastExp>(a.phys, rho.y()));
+      }
+      *reinterpret_cast<float2*>(ring_row + RO + xa + 2 * p) = psi2;
       if constexpr (kRegs) rho_next[p] = H;
     }
     if constexpr (kRegs) flag_next = flags_of(stb);
@@ -804,9 +828,11 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
           Fy = fma2(mg, sfy, F2::splat(a.phys.bfy));
         }
 
+        // A non-finite density turns the check sum into NaN (0 * inf and
+        // 0 * NaN are NaN); it is tested once, after the segment.  Columns
+        // beyond the lattice hold periodic images or zeroed padding.
+        nonfinite = fma2(rho, F2::splat(0.f), nonfinite);
         if (xp < a.nx) {
-          if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
-            atomicOr(a.status, kStatusNonFinite);
           if constexpr (MODE == kModeStep) {
             const F2 usx = fma2(Fx, inv_rho, ux);
             const F2 usy = fma2(Fy, inv_rho, uy);
@@ -966,12 +992,15 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
     }
   }
 
+  if (!(fabsf(nonfinite.x()) <= 3.0e38f) || !(fabsf(nonfinite.y()) <= 3.0e38f))
+    atomicOr(a.status, kStatusNonFinite);
   g = g0 + (uint32_t)K;
   if (*s_abort) {
     if (tid == kIss) {
       atomicOr(a.status, kStatusTimeout);
       for (int r = k; r < issued; ++r) {
         const uint32_t gr = g0 + (uint32_t)r;
+        if (a.extra_tx) mbar_complete_tx(&bars[gr % NS], a.extra_tx);
         mbar_wait_bounded(&bars[gr % NS], (gr / NS) & 1u, a.wait_ns);
       }
     }
@@ -1047,8 +1076,9 @@ struct BatchTile {
 // One time step of up to kBatchChunk lattices of a batch.  With PERSIST, CTA
 // b marches tiles [first[b], first[b + 1]) in order; otherwise CTA b marches
 // tile b (no loop state held across the march).  `parity` flips the
-// read/write buffers on alternate steps.
-template <int Q, typename S, int W, int NS, int MINB, bool PERSIST>
+// read/write buffers on alternate steps.  FL as for step_kernel (kFlExpPlain
+// when every member of the chunk has those settings).
+template <int Q, typename S, int W, int NS, int MINB, bool PERSIST, int FL>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     batch_step_kernel(const __grid_constant__ BatchArgs<typename Codec<S>::T, S> P,
                       const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
@@ -1064,7 +1094,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     const auto& a = P.a[tile.member][dir];
     if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(a);
     const auto* m = &members[tile.member];
-    return march_any<Q, S, W, NS, kModeStep, kFlRuntime>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
+    return march_any<Q, S, W, NS, kModeStep, FL>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
                                             tile.rows, tile.rev != 0, sm, g, policy);
   };
   if constexpr (PERSIST) {

@@ -90,3 +90,22 @@ def test_contact_angle_base_line_readings():
         want = math.degrees(math.acos((yb - yc) / R))
         assert abs(ca.theta_deg - want) < 0.3, (base, ca.theta_deg, want)
         assert abs(ca.y_base - yb) < 1e-12
+
+
+def test_contact_angles_of_several_drops_across_the_seam():
+    """Three caps of 50, 90 and 120 degrees, one straddling the periodic seam:
+    each is found and fitted on its own columns."""
+    nx, ny = 900, 200
+    phi, _, _ = W.wall_core_tail(W.wall_distance_slab(nx, ny), 3.0)
+    yb = A.surface_line(phi[:, 0], 0.5)
+    rho = np.full((ny, nx), 0.1)
+    want = []
+    for xc, th, R in ((20.0, 50.0, 60.0), (330.0, 90.0, 40.0), (640.0, 120.0, 30.0)):
+        yc = yb - R * math.cos(math.radians(th))
+        for shift in (-nx, 0, nx):
+            rho = np.maximum(rho, W.droplet_density(nx, ny, [(xc + shift, yc)], [R], 2.0, 0.1, 2.0))
+        want.append((xc, th))
+    got = A.contact_angles_of_drops(rho, phi, 2.0, 0.1, y_max=150)
+    assert len(got) == 3, got
+    for (xc, th), (gx, gth, _) in zip(sorted(want), got):
+        assert abs(((gx - xc + nx / 2) % nx) - nx / 2) < 1.0 and abs(gth - th) < 0.5, (xc, th, gx, gth)
