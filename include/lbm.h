@@ -117,9 +117,15 @@ typedef struct {
  * the paper's EOS parameters scaled by theta = 1/3, no body force. */
 int lbm_params_default(lbm_params* p);
 
-/* Creates a context.  a may be NULL (cudaMalloc is used); stream may be NULL
- * (the legacy default stream).  The population state is undefined until
- * lbm_set_populations or lbm_set_equilibrium succeeds.  *out is NULL on error. */
+/* Creates a context for one lattice with the problem statement of Sec. II
+ * (lattice and its Table I weights, tau of Eq. BE-BGK, the fluid-fluid coupling
+ * of Eq. force_SC, Eq. EOS, a uniform body force as in Sec. III A).  a may be
+ * NULL (cudaMalloc is used); stream may be NULL (the legacy default stream).
+ * The population state is undefined until lbm_set_populations or
+ * lbm_set_equilibrium succeeds.  *out is NULL on error.  Errors: LBM_EINVAL
+ * (p NULL, a size < 1, tau <= 0.5, an unknown lattice, storage, psi kind or
+ * rounding), LBM_ENOMEM (the allocator returned NULL; every block already
+ * obtained is returned to it), LBM_ECUDA. */
 int lbm_create(const lbm_params* p, const lbm_allocator* a, void* cuda_stream, lbm_ctx** out);
 
 /* Replaces the CUDA stream on which later calls enqueue work. */
@@ -145,13 +151,22 @@ int lbm_set_populations(lbm_ctx* c, const double* f);
 int lbm_set_equilibrium(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
                         const double* dfi);
 
-/* Advances nsteps >= 0 time steps (one fused kernel launch per step).  Returns
- * after enqueueing, or LBM_ENONFINITE when check_every > 0 and a check found a
- * non-finite density (the state is then kept as it was after that step). */
+/* Advances nsteps >= 0 time steps (one fused kernel launch per step): the
+ * update of Sec. II per node -- streaming, Eqs. M0 and M1, psi (Eq. EOS or
+ * the exponential form), F_FF (Eq. force_SC), F_FS and Delta F_S (Eqs.
+ * force_SC_FS, wall_shift), the optional projection (after Eq. f2) and the
+ * EDM-BGK collision (Eq. BE-BGK with the shifted-velocity equilibrium of
+ * Sec. II B).  Returns after enqueueing, or LBM_ENONFINITE when check_every > 0
+ * and a check found a non-finite density (the state is then kept as it was
+ * after that step), or LBM_ETIMEOUT when a bounded device wait gave up.
+ * Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (no populations set yet, or a
+ * poisoned context), LBM_ECUDA. */
 int lbm_step(lbm_ctx* c, int64_t nsteps);
 
-/* Reads rho and the reported velocity u = (j + F/2) / rho of the current state
- * into host arrays [ny][nx] (any may be NULL).  Synchronises the stream. */
+/* Reads rho (Eq. M0) and the reported velocity u = (j + F/2) / rho (j of Eq.
+ * M1, F the total force of the step) of the current state into host arrays
+ * [ny][nx] (any may be NULL).  Synchronises the stream.  Errors: LBM_ESTATE,
+ * LBM_ECUDA. */
 int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy);
 
 /* As lbm_moments, but into DEVICE arrays of ny*nx doubles, enqueued on the
@@ -171,12 +186,16 @@ int lbm_steps_done(const lbm_ctx* c, int64_t* out);
 /* Waits for all work enqueued by this context. */
 int lbm_sync(lbm_ctx* c);
 
-/* Frees the context and its device memory; NULL is accepted.  Always LBM_OK. */
+/* Frees the context and its device memory (returned through the allocator it
+ * came from); NULL is accepted.  Always LBM_OK.  No paper passage: resource
+ * management of the library. */
 int lbm_destroy(lbm_ctx* c);
 
 /* Human-readable description of the last error on c ("" if none), owned by c.
  * lbm_last_error(NULL) reports errors of calls that had no context yet. */
 const char* lbm_last_error(const lbm_ctx* c);
+
+/* ---- test hook (failure detection; not part of the modelling API) -------- */
 
 /* Test hook for failure detection: arms the next lbm_step so that every
  * shared-memory stage of its kernel expects 16 bytes more than its copies

@@ -204,6 +204,8 @@ class DynamicAngles:
     front: tuple
     rear: tuple
     npoints: tuple
+    theta_adv_hR_deg: float = float("nan")
+    theta_rec_hR_deg: float = float("nan")
 
 
 def dynamic_angles(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
@@ -212,7 +214,9 @@ def dynamic_angles(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: floa
     the interface contour rho = (rho_l + rho_v)/2 in the hydrodynamic region is
     split at the apex; one circle is fitted to the points ahead of it (front)
     and one to those behind it (rear), and each angle is acos((y_b - y_c)/R)
-    with y_b the solid surface phi_S = 0.5 (Sec. III C)."""
+    with y_b the solid surface phi_S = 0.5 (Sec. III C).  Also returned, as
+    theta_*_hR_deg: acos(1 - h/R) with the common apex height h above y_b and
+    each circle's radius R (the wording of the Fig. 9 caption)."""
     ny, nx = rho.shape
     shift = recenter_x(rho, 0.5 * (rho_l + rho_v))
     rho = np.roll(rho, shift, axis=1)
@@ -233,8 +237,11 @@ def dynamic_angles(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: floa
         xc, yc, R = fit_circle(x[sel], y[sel])
         c = max(-1.0, min(1.0, (yb - yc) / R))
         out.append((math.degrees(math.acos(c)), (xc - shift) % nx, yc, R))
-    return DynamicAngles(out[0][0], out[1][0], (xa - shift) % nx, float(y[ia] - yb),
-                         out[0][1:], out[1][1:], (int(front.sum()), int(rear.sum())))
+    h = float(y[ia] - yb)
+    hr = [math.degrees(math.acos(max(-1.0, min(1.0, 1.0 - h / o[3])))) for o in out]
+    return DynamicAngles(out[0][0], out[1][0], (xa - shift) % nx, h,
+                         out[0][1:], out[1][1:], (int(front.sum()), int(rear.sum())),
+                         hr[0], hr[1])
 
 
 def drop_velocity(rho: np.ndarray, ux: np.ndarray, rho_mid: float, phi_s=None) -> float:
@@ -247,29 +254,31 @@ def drop_velocity(rho: np.ndarray, ux: np.ndarray, rho_mid: float, phi_s=None) -
 
 
 def contact_angles_of_drops(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
-                            y_max: int | None = None, min_width: int = 12):
+                            y_max: int | None = None, min_width: int = 12,
+                            min_height: int = 3):
     """Static angles of every drop resting on the bottom wall of a periodic
-    lattice holding many of them: the liquid above the solid surface (rho
-    above the mid density, phi_S < 0.5, below ``y_max``) is split into
-    connected pieces (periodic in x), and each piece at least ``min_width``
-    columns wide gets the circle fit of ``contact_angle`` over its own columns.
-    Returns a list of (x_centre, theta_deg, R), sorted by x_centre."""
-    from scipy import ndimage
+    lattice holding many of them.  A column belongs to a drop when at least
+    ``min_height`` of its nodes in the hydrodynamic region (phi_S < 0.01, below
+    ``y_max``) are liquid (rho above the mid density), so a wetting film along
+    the wall does not join the drops; each periodic run of such columns at
+    least ``min_width`` wide gets the circle fit of ``contact_angle`` over its
+    own columns.  Returns a list of (x_centre, theta_deg, R), sorted by
+    x_centre."""
     ny, nx = rho.shape
     y_max = ny // 2 if y_max is None else y_max
     mid = 0.5 * (rho_l + rho_v)
-    liquid = (rho > mid) & (phi_s < 0.5)
+    liquid = (rho > mid) & (phi_s < 0.01)
     liquid[y_max:, :] = False
-    cols = liquid.any(axis=0)
-    if cols.all():
-        raise ValueError("liquid spans every column: no drop boundary")
+    cols = liquid.sum(axis=0) >= min_height
+    if cols.all() or not cols.any():
+        raise ValueError("no separate drops: every column or none holds liquid")
     shift = -int(np.argmin(cols))          # roll a dry column to x = 0
+    cols = np.roll(cols, shift)
     rho_r = np.roll(rho, shift, axis=1)
     phi_r = np.roll(phi_s, shift, axis=1)
-    lab, n = ndimage.label(np.roll(liquid, shift, axis=1))
+    edges = np.flatnonzero(np.diff(np.concatenate(([0], cols.astype(np.int8), [0]))))
     out = []
-    for sl in ndimage.find_objects(lab):
-        x0, x1 = sl[1].start, sl[1].stop
+    for x0, x1 in zip(edges[0::2], edges[1::2]):
         if x1 - x0 < min_width:
             continue
         try:

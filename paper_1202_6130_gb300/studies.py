@@ -318,9 +318,10 @@ def dynamic_angles(steps_static: int = 60000, steps: int = 100000, chunk: int = 
             try:
                 d = analysis.dynamic_angles(rho, phi, rho_l, rho_v, y_max=ny - 10)
                 U = analysis.drop_velocity(rho, ux, 0.5 * (rho_l + rho_v), phi)
-                hist[i].append((done, d.theta_adv_deg, d.theta_rec_deg, U))
+                hist[i].append((done, d.theta_adv_deg, d.theta_rec_deg, U, d.theta_adv_hR_deg,
+                                d.theta_rec_hR_deg))
             except Exception:
-                hist[i].append((done, float("nan"), float("nan"), float("nan")))
+                hist[i].append((done,) + (float("nan"),) * 5)
 
     t0 = time.perf_counter()
     _run_batch(sims, steps, chunk, record)
@@ -329,7 +330,8 @@ def dynamic_angles(steps_static: int = 60000, steps: int = 100000, chunk: int = 
         last, prev = h[-1], h[-2] if len(h) > 1 else h[-1]
         out["runs"].append({"G_R": GR, "G_A": GA, "epsilon": eps, "dp": dp, "U": last[3],
                             "Ca": last[3] * mu_l / gamma, "theta_adv_deg": last[1],
-                            "theta_rec_deg": last[2],
+                            "theta_rec_deg": last[2], "theta_adv_hR_deg": last[4],
+                            "theta_rec_hR_deg": last[5],
                             "theta_adv_change_last_chunk": last[1] - prev[1],
                             "theta_rec_change_last_chunk": last[2] - prev[2], "history": h})
         sims[i].close()

@@ -68,6 +68,8 @@ def test_dynamic_angles_of_two_joined_circular_arcs():
     for shift in (0, 320):
         d = A.dynamic_angles(np.roll(dens, shift, axis=1), phi, 1.0, 0.1)
         assert abs(d.theta_adv_deg - 70.0) < 1.0 and abs(d.theta_rec_deg - 50.0) < 1.0, d
+        # the same arcs through the common apex: acos(1 - h/R) gives the same angles
+        assert abs(d.theta_adv_hR_deg - 70.0) < 1.0 and abs(d.theta_rec_hR_deg - 50.0) < 1.0, d
 
 
 def test_contact_angle_base_line_readings():
