@@ -253,6 +253,23 @@ def drop_velocity(rho: np.ndarray, ux: np.ndarray, rho_mid: float, phi_s=None) -
     return float((rho[m] * ux[m]).sum() / rho[m].sum())
 
 
+def _liquid_runs(rho, phi_s, rho_l, rho_v, y_max, min_height):
+    """Periodic runs of columns with at least ``min_height`` liquid nodes in the
+    hydrodynamic region (phi_S < 0.01, below y_max): the columns under drops or
+    ridges, not those under a wetting film alone.  Returns (shift, runs) with
+    the runs [x0, x1) in a frame rolled by ``shift`` so that none wraps."""
+    mid = 0.5 * (rho_l + rho_v)
+    liquid = (rho > mid) & (phi_s < 0.01)
+    liquid[y_max:, :] = False
+    cols = liquid.sum(axis=0) >= min_height
+    if cols.all() or not cols.any():
+        raise ValueError("no separate drops: every column or none holds liquid")
+    shift = -int(np.argmin(cols))          # roll a dry column to x = 0
+    cols = np.roll(cols, shift)
+    edges = np.flatnonzero(np.diff(np.concatenate(([0], cols.astype(np.int8), [0]))))
+    return shift, list(zip(edges[0::2].tolist(), edges[1::2].tolist()))
+
+
 def contact_angles_of_drops(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
                             y_max: int | None = None, min_width: int = 12,
                             min_height: int = 3):
@@ -266,19 +283,11 @@ def contact_angles_of_drops(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rh
     x_centre."""
     ny, nx = rho.shape
     y_max = ny // 2 if y_max is None else y_max
-    mid = 0.5 * (rho_l + rho_v)
-    liquid = (rho > mid) & (phi_s < 0.01)
-    liquid[y_max:, :] = False
-    cols = liquid.sum(axis=0) >= min_height
-    if cols.all() or not cols.any():
-        raise ValueError("no separate drops: every column or none holds liquid")
-    shift = -int(np.argmin(cols))          # roll a dry column to x = 0
-    cols = np.roll(cols, shift)
+    shift, runs = _liquid_runs(rho, phi_s, rho_l, rho_v, y_max, min_height)
     rho_r = np.roll(rho, shift, axis=1)
     phi_r = np.roll(phi_s, shift, axis=1)
-    edges = np.flatnonzero(np.diff(np.concatenate(([0], cols.astype(np.int8), [0]))))
     out = []
-    for x0, x1 in zip(edges[0::2], edges[1::2]):
+    for x0, x1 in runs:
         if x1 - x0 < min_width:
             continue
         try:
@@ -287,4 +296,32 @@ def contact_angles_of_drops(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rh
         except ValueError:
             continue
         out.append((float((c.xc - shift) % nx), c.theta_deg, c.R))
+    return sorted(out)
+
+
+def contact_line_angles(rho: np.ndarray, phi_s: np.ndarray, rho_l: float, rho_v: float,
+                        y_max: int | None = None, window: int = 40, min_height: int = 3):
+    """Angle at every contact line of a periodic lattice whose drops may have
+    merged into ridges: for each end of each run of liquid columns (see
+    ``contact_angles_of_drops``), a circle is fitted to the interface contour
+    over the ``window`` columns next to the line (hydrodynamic region only),
+    and the angle is acos((y_b - y_c)/R) with y_b the solid surface.  Returns a
+    list of (x_line, side, theta_deg) sorted by x_line, side -1 for a left
+    (rising) and +1 for a right (falling) contact line."""
+    ny, nx = rho.shape
+    y_max = ny // 2 if y_max is None else y_max
+    shift, runs = _liquid_runs(rho, phi_s, rho_l, rho_v, y_max, min_height)
+    rho_r = np.roll(rho, shift, axis=1)
+    phi_r = np.roll(phi_s, shift, axis=1)
+    out = []
+    for x0, x1 in runs:
+        if x1 - x0 < window:
+            continue
+        for side, xr in ((-1, (max(0, x0 - 3), x0 + window)), (+1, (x1 - window, min(nx, x1 + 3)))):
+            try:
+                c = contact_angle(rho_r, phi_r, rho_l, rho_v, x_range=xr, y_max=y_max)
+            except ValueError:
+                continue
+            xl = x0 if side < 0 else x1
+            out.append((float((xl - shift) % nx), side, c.theta_deg))
     return sorted(out)

@@ -133,24 +133,35 @@ def slip_study(storages=STORAGES, nx: int = 8, ny: int = 256, steps: int = 30000
     return out
 
 
+def _interface_height(rho, mid):
+    """Height of the topmost liquid node per column (-1 where none)."""
+    liquid = rho > mid
+    ny = rho.shape[0]
+    top = ny - 1 - np.argmax(liquid[::-1, :], axis=0)
+    return np.where(liquid.any(axis=0), top, -1)
+
+
 def large_precision(storages=("fp32", "fp16s", "bf16s", "fp16s-rn", "bf16s-rn"), steps: int = 20000):
     """8192x4096 multi-drop lattice: each storage precision against FP64 storage
-    after `steps` steps: mass drift, density differences, and the static angle
-    of every drop (the caps that merged count as one drop) against the same
-    drop in FP64."""
+    after `steps` steps: mass drift, density differences, the liquid height of
+    every column, and the angle at every contact line (the 64 caps overlap from
+    the start and merge into ridges, so the angles are those of the ridge ends,
+    each from a circle fitted to the 40 columns next to the line), matched to
+    the same line in FP64."""
     import workloads as W
     w = W.large_multi_droplet(noise_amp=0.0)
     rho_l, rho_v = w.meta["rho_l"], w.meta["rho_v"]
+    mid = 0.5 * (rho_l + rho_v)
     ref = Simulation.from_workload(w, storage="fp64")
     m0 = ref.totals()[0]
     t0 = time.perf_counter()
     ref.step(steps)
     rho64 = ref.moments()[0]
     t64 = time.perf_counter() - t0
-    drops64 = analysis.contact_angles_of_drops(rho64, w.phi_s, rho_l, rho_v, y_max=400)
+    lines64 = analysis.contact_line_angles(rho64, w.phi_s, rho_l, rho_v, y_max=400)
+    h64 = _interface_height(rho64[:400], mid)
     out = {"steps": steps, "fp64": {"mass_drift_rel": (ref.totals()[0] - m0) / m0, "wall_s": t64,
-                                    "drops": len(drops64),
-                                    "theta_deg": [d[1] for d in drops64]}}
+                                    "contact_lines": lines64}}
     ref.close()
     for st in storages:
         sim = Simulation.from_workload(w, **storage_kw(st))
@@ -159,19 +170,26 @@ def large_precision(storages=("fp32", "fp16s", "bf16s", "fp16s-rn", "bf16s-rn"),
         rho = sim.moments()[0]
         b = sim.totals()[0]
         d = np.abs(rho - rho64)
-        drops = analysis.contact_angles_of_drops(rho, w.phi_s, rho_l, rho_v, y_max=400)
+        try:
+            lines = analysis.contact_line_angles(rho, w.phi_s, rho_l, rho_v, y_max=400)
+        except ValueError:
+            lines = []
         errs = []
-        for xc, th, _ in drops:
-            dx = [abs(((xc - x64 + w.nx / 2) % w.nx) - w.nx / 2) for x64, _, _ in drops64]
-            k = int(np.argmin(dx))
-            if dx[k] < 5.0:
-                errs.append(th - drops64[k][1])
+        for xl, side, th in lines:
+            for x64, s64, th64 in lines64:
+                dx = abs(((xl - x64 + w.nx / 2) % w.nx) - w.nx / 2)
+                if s64 == side and dx <= 5:
+                    errs.append(th - th64)
+                    break
+        dh = np.abs(_interface_height(rho[:400], mid) - h64)
         out[st] = {"mass_drift_rel": (b - a) / a, "mass_vs_fp64_rel": (b - m0) / m0,
                    "rho_max_abs_err": float(d.max()), "rho_mean_abs_err": float(d.mean()),
                    "rho_rms_err": float(np.sqrt((d * d).mean())),
-                   "drops_matched": len(errs), "drops": len(drops),
+                   "contact_lines": lines, "contact_lines_matched": len(errs),
                    "theta_max_abs_err_vs_fp64_deg": float(np.max(np.abs(errs))) if errs else float("nan"),
                    "theta_err_vs_fp64_deg": errs,
+                   "liquid_height_max_abs_diff": int(dh.max()),
+                   "liquid_height_columns_differing": int((dh > 0).sum()),
                    "finite": bool(np.isfinite(rho).all())}
         sim.close()
     return out
@@ -345,6 +363,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--storages", default=None, help="comma-separated storage modes")
     ap.add_argument("--size", default=None, help="lattice NXxNY (sweep, slip)")
+    ap.add_argument("--surfaces", default=None,
+                    help="dynamic: surfaces as 'G_R,G_A,eps;G_R,G_A,eps;...'")
     ap.add_argument("--out", default=None, help="also write the JSON object to this file")
     args = ap.parse_args(argv)
     import torch
@@ -354,6 +374,9 @@ def main(argv=None):
         kw["steps"] = args.steps
     if args.storages and args.which not in ("paper", "dynamic"):
         kw["storages"] = tuple(args.storages.split(","))
+    if args.surfaces and args.which == "dynamic":
+        kw["surfaces"] = tuple(tuple(float(v) for v in t.split(","))
+                               for t in args.surfaces.split(";"))
     if args.size and args.which in ("sweep", "slip"):
         kw["nx"], kw["ny"] = (int(v) for v in args.size.lower().split("x"))
     fn = {"sweep": contact_angle_sweep, "slip": slip_study, "large": large_precision,

@@ -111,3 +111,18 @@ def test_contact_angles_of_several_drops_across_the_seam():
     assert len(got) == 3, got
     for (xc, th), (gx, gth, _) in zip(sorted(want), got):
         assert abs(((gx - xc + nx / 2) % nx) - nx / 2) < 1.0 and abs(gth - th) < 0.5, (xc, th, gx, gth)
+
+
+def test_contact_line_angles_at_the_ends_of_a_ridge():
+    """A ridge made of two overlapping caps of 70 degrees: the angle at each of
+    its two contact lines is that of the cap ending there."""
+    nx, ny = 700, 200
+    phi, _, _ = W.wall_core_tail(W.wall_distance_slab(nx, ny), 3.0)
+    yb = A.surface_line(phi[:, 0], 0.5)
+    R = 60.0
+    yc = yb - R * math.cos(math.radians(70.0))
+    rho = W.droplet_density(nx, ny, [(300.0, yc), (380.0, yc)], [R, R], 2.0, 0.1, 2.0)
+    lines = A.contact_line_angles(rho, phi, 2.0, 0.1, y_max=150)
+    assert [s for _, s, _ in lines] == [-1, 1], lines
+    for _, _, th in lines:
+        assert abs(th - 70.0) < 1.0, lines
