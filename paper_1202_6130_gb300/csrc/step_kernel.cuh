@@ -630,7 +630,6 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
   // row whose psi was just formed, collided in the next iteration.
   F2 fnext[kRegs ? P : 1][kRegs ? Q : 1];
   F2 rho_next[P];
-  F2 nonfinite = F2::splat(0.f);
   uint32_t flag_next = 0;
   int s = (int)(g0 % NS);
   uint32_t phase = (g0 / NS) & 1u;
@@ -828,11 +827,9 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
           Fy = fma2(mg, sfy, F2::splat(a.phys.bfy));
         }
 
-        // A non-finite density turns the check sum into NaN (0 * inf and
-        // 0 * NaN are NaN); it is tested once, after the segment.  Columns
-        // beyond the lattice hold periodic images or zeroed padding.
-        nonfinite = fma2(rho, F2::splat(0.f), nonfinite);
         if (xp < a.nx) {
+          if (!(fabsf(rho.x()) <= 3.0e38f) || (pair_ok && !(fabsf(rho.y()) <= 3.0e38f)))
+            atomicOr(a.status, kStatusNonFinite);
           if constexpr (MODE == kModeStep) {
             const F2 usx = fma2(Fx, inv_rho, ux);
             const F2 usy = fma2(Fy, inv_rho, uy);
@@ -992,8 +989,6 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
     }
   }
 
-  if (!(fabsf(nonfinite.x()) <= 3.0e38f) || !(fabsf(nonfinite.y()) <= 3.0e38f))
-    atomicOr(a.status, kStatusNonFinite);
   g = g0 + (uint32_t)K;
   if (*s_abort) {
     if (tid == kIss) {
