@@ -183,6 +183,22 @@ int lbm_totals(lbm_ctx* c, double out[3]);
 /* Steps taken since the populations were last set. */
 int lbm_steps_done(const lbm_ctx* c, int64_t* out);
 
+/* The context's clock, for checkpoint and resume: the steps taken since the
+ * populations were last set, and the counter from which stochastic rounding
+ * draws the random bits of the next step (16-bit storage: the bits are a hash
+ * of the node and this counter).  lbm_get_clock also reports the shift
+ * density rho_s of 16-bit storage (0 otherwise; rho_s may be NULL).  A
+ * checkpoint is the populations (lbm_get_populations) plus these numbers.  To
+ * resume, create a context with the same parameters and shift_rho = rho_s,
+ * then lbm_set_populations and lbm_set_clock: it steps on bit for bit as the
+ * original would have, in every storage (16-bit values survive the FP64 round
+ * trip exactly).  No paper passage: state management of the library.
+ * lbm_get_clock synchronises the stream.  Errors: LBM_EINVAL (null steps or
+ * counter output, negative steps), LBM_ESTATE (no populations set),
+ * LBM_ECUDA. */
+int lbm_get_clock(lbm_ctx* c, int64_t* steps, uint32_t* rounding_counter, double* rho_s);
+int lbm_set_clock(lbm_ctx* c, int64_t steps, uint32_t rounding_counter);
+
 /* Waits for all work enqueued by this context. */
 int lbm_sync(lbm_ctx* c);
 

@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 from ctypes import (POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t,
-                    c_uint8, c_void_p)
+                    c_uint32, c_uint8, c_void_p)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
@@ -71,6 +71,8 @@ SIGNATURES = {
     "lbm_get_populations": (c_int, [c_void_p, _DP]),
     "lbm_totals": (c_int, [c_void_p, _DP]),
     "lbm_steps_done": (c_int, [c_void_p, POINTER(c_int64)]),
+    "lbm_get_clock": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_uint32), _DP]),
+    "lbm_set_clock": (c_int, [c_void_p, c_int64, c_uint32]),
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_destroy": (c_int, [c_void_p]),
     "lbm_last_error": (c_char_p, [c_void_p]),

@@ -677,6 +677,35 @@ int lbm_steps_done(const lbm_ctx* c, int64_t* out) {
   return LBM_OK;
 }
 
+int lbm_get_clock(lbm_ctx* c, int64_t* steps, uint32_t* rounding_counter, double* rho_s) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!steps || !rounding_counter) return fail(c, LBM_EINVAL, "null output");
+  if (rho_s) *rho_s = c->rho_s;
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  uint32_t h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->d_status + kRngWord + c->cur, sizeof h, cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  *steps = c->steps;
+  *rounding_counter = h;
+  return LBM_OK;
+}
+
+int lbm_set_clock(lbm_ctx* c, int64_t steps, uint32_t rounding_counter) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (steps < 0) return fail(c, LBM_EINVAL, "negative step count");
+  if (!c->has_state) return fail(c, LBM_ESTATE, "populations not set");
+  // The next step reads the counter word of the current buffer (see make_args).
+  const uint32_t v = rounding_counter;
+  CK(c, cudaMemcpyAsync(c->d_status + kRngWord + c->cur, &v, sizeof v, cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->steps = steps;
+  return LBM_OK;
+}
+
 int lbm_sync(lbm_ctx* c) {
   int rc = guard(c);
   if (rc) return rc;

@@ -165,6 +165,65 @@ class Simulation:
         self._chk(self.lib.lbm_steps_done(self.ctx, ctypes.byref(v)))
         return v.value
 
+    def clock(self):
+        """(steps since the populations were set, stochastic-rounding counter,
+        shift density rho_s of 16-bit storage or 0)."""
+        st, rc, rs = ctypes.c_int64(), ctypes.c_uint32(), ctypes.c_double()
+        self._chk(self.lib.lbm_get_clock(self.ctx, ctypes.byref(st), ctypes.byref(rc),
+                                         ctypes.byref(rs)))
+        return st.value, rc.value, rs.value
+
+    def checkpoint(self) -> dict:
+        """The state needed to resume bit for bit: the parameters this object
+        was created with, the populations (FP64, the layout of
+        set_populations) and the clock.  The wall fields are the caller's
+        static inputs; set them again on the restored simulation."""
+        steps, counter, rho_s = self.clock()
+        p = self.params
+        params = {k: getattr(p, k) for k, _ in L.lbm_params._fields_ if k != "body_force"}
+        params["body_force"] = (p.body_force[0], p.body_force[1])
+        return {"populations": self.populations(), "steps": steps, "rounding_counter": counter,
+                "rho_s": rho_s, "params": params}
+
+    def restore(self, ckpt: dict):
+        """Sets the populations and the clock of a checkpoint.  Bit for bit
+        only if this simulation has the checkpoint's parameters and, for
+        16-bit storage, its shift density (``from_checkpoint`` makes one)."""
+        self.set_populations(ckpt["populations"])
+        self._chk(self.lib.lbm_set_clock(self.ctx, int(ckpt["steps"]),
+                                         int(ckpt["rounding_counter"])))
+
+    def save(self, path: str):
+        """Writes checkpoint() to an .npz file."""
+        c = self.checkpoint()
+        params = c.pop("params")
+        np.savez(path, **c, **{"param_" + k: np.asarray(v) for k, v in params.items()})
+
+    @staticmethod
+    def read_checkpoint(path: str) -> dict:
+        with np.load(path) as z:
+            c = {k: z[k] for k in z.files if not k.startswith("param_")}
+            c["params"] = {k[6:]: z[k].tolist() for k in z.files if k.startswith("param_")}
+        return c
+
+    @classmethod
+    def from_checkpoint(cls, ckpt, **kw):
+        """A new simulation with a checkpoint's parameters (the shift density
+        included), its populations and its clock.  ``ckpt``: a dict of
+        checkpoint() or the path of a save() file.  Walls: call set_wall."""
+        if isinstance(ckpt, str):
+            ckpt = cls.read_checkpoint(ckpt)
+        p = dict(ckpt["params"])
+        eos = (p["eos_theta_v"], p["eos_theta_u"], p["eos_theta_l"], p["eos_rho1"], p["eos_rho2"])
+        sim = cls(int(p["nx"]), int(p["ny"]), lattice=int(p["lattice"]), storage=int(p["storage"]),
+                  tau=p["tau"], G=p["G"], rho0=p["rho0"], psi_kind=int(p["psi_kind"]),
+                  project=bool(p["project"]), body_force=tuple(p["body_force"]),
+                  shift_rho=float(ckpt["rho_s"]) if float(ckpt["rho_s"]) > 0 else p["shift_rho"],
+                  eos=eos, check_every=int(p["check_every"]), tile_rows=int(p["tile_rows"]),
+                  rounding=int(p["rounding"]), **kw)
+        sim.restore(ckpt)
+        return sim
+
     def layout(self) -> dict:
         lay = L.lbm_layout()
         self._chk(self.lib.lbm_get_layout(self.ctx, ctypes.byref(lay)))
