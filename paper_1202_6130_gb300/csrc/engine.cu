@@ -973,10 +973,17 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
       for (int d = 0; d < 2; ++d)
         pa->a[i][d] = make_args<Q, S>(c, d, static_cast<S*>(c->buf[d ^ 1]), nullptr, nullptr, nullptr, 0);
       pa->cur[i] = c->cur;
+      // Segments of about L rows, balanced over the member's height: a short
+      // remainder segment would pay its 2R halo rows and its pipeline fill
+      // for a few rows only.
       const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
-      for (int y0 = 0; y0 < c->p.ny; y0 += L)
+      const int nseg = std::max(1, (c->p.ny + L / 2) / L);
+      for (int j = 0; j < nseg; ++j) {
+        const int y0 = (int)((int64_t)c->p.ny * j / nseg);
+        const int y1 = (int)((int64_t)c->p.ny * (j + 1) / nseg);
         for (int x0 = 0; x0 < c->p.nx; x0 += W)
-          ctiles[k].push_back({i, x0, y0, std::min(L, c->p.ny - y0), (y0 / L) & 1});
+          ctiles[k].push_back({i, x0, y0, y1 - y0, j & 1});
+      }
     }
     total += ctiles[k].size();
   }
