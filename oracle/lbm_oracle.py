@@ -27,6 +27,17 @@ the design notes of the repository):
     density; u* = u + rho g dt / rho (exact difference method).
   * The optional projection (Eq. f2) acts after streaming, before collision.
   * Reported velocity u_phys = (j + F/2) / rho.
+
+What pins it (tests/test_oracle_pins.py): Table I exactly, the equilibrium
+moments, the EDM closed form at tau = 1, streaming, the force operator against
+an O(N^2) brute-force pair sum, conservation laws, the flat film, Laplace's
+law, the Poiseuille curvature, Couette flow, coexistence densities, the
+adsorbed-fraction trend of Sec. III and the trend of the contact angle with
+G_A.  Parity unpinned: the magnitude of the fluid-solid terms under the
+readings above (the sign of psi_FS, the F_FF term of Delta u_wall, rho rather
+than psi multiplying the long-range sum) is pinned in sign and trend only; with
+them the paper's own fluid and walls give static angles 8-35 degrees below the
+table printed in Sec. III B, and no reading tried reproduces it.
 """
 from __future__ import annotations
 
