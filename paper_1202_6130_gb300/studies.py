@@ -202,9 +202,27 @@ PAPER_THETA = {0.0: 150.0, 0.2: 112.0, 0.5: 58.7, 0.7: 36.7, 0.8: 30.9, 0.9: 24.
 BASES = ("surface", "outer", "interface")
 
 
+def paper_wall_functions(solid, mode: str = "iterate", n_rep: int = 5, n_att: int = 22):
+    """Wall functions of the Appendix for a solid mask, D2Q21.  "iterate": the
+    reading the oracle and the library take, G^(n) = one filter pass of
+    G^(n-1) reset to one on the solid, psi_R-bar = G^(5), psi_A-bar = G^(22) -
+    G^(5), phi_S = G^(22).  "mean": the printed outer sum over passes read as
+    the mean of the iterates G^(1) .. G^(N) (a sum would exceed one, which a
+    wall probability cannot), each function then built from those means; every
+    iterate comes from the library's filter."""
+    if mode == "iterate":
+        return wall_gaussian_filter(solid, lattice=21, n_rep=n_rep, n_att=n_att)
+    if mode != "mean":
+        raise ValueError(mode)
+    its = [wall_gaussian_filter(solid, lattice=21, n_rep=n, n_att=n)[0] for n in range(1, n_att + 1)]
+    g_r = np.mean(its[:n_rep], axis=0)
+    g_a = np.mean(its, axis=0)
+    return g_a, g_r, g_a - g_r
+
+
 def paper_drops(cases, steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
                 nx: int = 650, ny: int = 150, G_R: float = 1.33, tau: float = 1.0,
-                solid_rows: int = 1):
+                solid_rows: int = 1, filter_mode: str = "iterate"):
     """Sessile drops of the paper's fluid and walls, one per (R0, G_A) in
     ``cases``, advanced together in one batch: D2Q21, Eq. EOS (theta_V =
     theta/4, theta_U = -theta/4, theta_L = theta, rho_1 = 0.222, rho_2 =
@@ -214,12 +232,13 @@ def paper_drops(cases, steps: int = 100000, chunk: int = 20000, storage: str = "
     Per case: the static angle on each base line of ``analysis.contact_angle``
     (the solid surface, the domain's outer boundary, the bottom liquid-vapour
     interface) and its history.  Readings (1/theta in the force, the sign of
-    psi_FS) are the ones the oracle uses."""
+    psi_FS) are the ones the oracle uses; filter_mode selects the reading of the
+    Appendix filter (paper_wall_functions)."""
     import workloads as W
     th = 2.0 / 3.0
     solid = np.zeros((ny, nx), bool)
     solid[:solid_rows, :] = True
-    phi, pr, pa = wall_gaussian_filter(solid, lattice=21, n_rep=5, n_att=22)
+    phi, pr, pa = paper_wall_functions(solid, filter_mode)
     yb = analysis.surface_line(phi[:, 0], 0.5)
     rho_l, rho_v = 1.0, 0.1
     sims = []
@@ -256,12 +275,14 @@ def paper_drops(cases, steps: int = 100000, chunk: int = 20000, storage: str = "
     for s in sims:
         s.close()
     return {"nx": nx, "ny": ny, "G_R": G_R, "steps": steps, "storage": storage,
-            "wall_s": wall, "y_surface": yb, "rows": rows}
+            "filter_mode": filter_mode, "wall_s": wall, "y_surface": yb,
+            "y_hydrodynamic": analysis.surface_line(phi[:, 0], 0.01), "rows": rows}
 
 
 def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "fp32",
                       nx: int = 650, ny: int = 150, R0: float = 50.0, G_R: float = 1.33,
-                      tau: float = 1.0, solid_rows: int = 1, R0_others=(30.0, 65.0)):
+                      tau: float = 1.0, solid_rows: int = 1, R0_others=(30.0, 65.0),
+                      filter_mode: str = "iterate"):
     """The static angle against G_A at G_R = 1.33 (Sec. III B, Figs. 6-7) next
     to the printed angles, at R0 = ``R0``; and, for the angles the domain
     holds at every size (G_A = 0-0.7), at the drop sizes ``R0_others`` too
@@ -269,7 +290,7 @@ def paper_theta_table(steps: int = 100000, chunk: int = 20000, storage: str = "f
     cases = [(R0, ga) for ga in PAPER_THETA]
     cases += [(r, ga) for r in R0_others for ga in PAPER_THETA if ga <= 0.7]
     out = paper_drops(cases, steps=steps, chunk=chunk, storage=storage, nx=nx, ny=ny, G_R=G_R,
-                      tau=tau, solid_rows=solid_rows)
+                      tau=tau, solid_rows=solid_rows, filter_mode=filter_mode)
     for r in out["rows"]:
         r["paper_theta_deg"] = PAPER_THETA[r["G_A"]]
         r["diff_deg"] = r["theta_deg"]["surface"] - PAPER_THETA[r["G_A"]]
@@ -289,7 +310,7 @@ def dynamic_angles(steps_static: int = 60000, steps: int = 100000, chunk: int = 
                    dps=(0.175e-4, 1.75e-4, 3.5e-4, 5.25e-4),
                    surfaces=((1.33, 0.5, 1.0), (0.9, 0.42, 1.0), (1.33, 0.57, 1.3)),
                    storage: str = "fp32", nx: int = 650, ny: int = 150, R0: float = 50.0,
-                   tau: float = 1.0, gamma: float = 0.09):
+                   tau: float = 1.0, gamma: float = 0.09, filter_mode: str = "iterate"):
     """Contact-angle dynamics of Sec. III C: each surface (G_R, G_A, epsilon)
     first relaxes a static drop; the relaxed populations then restart under a
     uniform force density dp / nx along +x (a pressure difference dp over the
@@ -301,12 +322,12 @@ def dynamic_angles(steps_static: int = 60000, steps: int = 100000, chunk: int = 
     th = 2.0 / 3.0
     solid = np.zeros((ny, nx), bool)
     solid[0, :] = True
-    phi, pr, pa = wall_gaussian_filter(solid, lattice=21, n_rep=5, n_att=22)
+    phi, pr, pa = paper_wall_functions(solid, filter_mode)
     yb = analysis.surface_line(phi[:, 0], 0.5)
     rho_l, rho_v = 1.0, 0.1
     mu_l = rho_l * th * (tau - 0.5)
     out = {"nx": nx, "ny": ny, "R0": R0, "tau": tau, "gamma": gamma, "storage": storage,
-           "steps_static": steps_static, "steps": steps, "runs": []}
+           "filter_mode": filter_mode, "steps_static": steps_static, "steps": steps, "runs": []}
     statics = []
     for (GR, GA, eps) in surfaces:
         s = _paper_sim(nx, ny, storage, tau, GR, GA, eps, phi, pr, pa)
@@ -363,6 +384,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--storages", default=None, help="comma-separated storage modes")
     ap.add_argument("--size", default=None, help="lattice NXxNY (sweep, slip)")
+    ap.add_argument("--filter", default=None, choices=["iterate", "mean"],
+                    help="paper: reading of the Appendix filter")
     ap.add_argument("--surfaces", default=None,
                     help="dynamic: surfaces as 'G_R,G_A,eps;G_R,G_A,eps;...'")
     ap.add_argument("--out", default=None, help="also write the JSON object to this file")
@@ -374,6 +397,8 @@ def main(argv=None):
         kw["steps"] = args.steps
     if args.storages and args.which not in ("paper", "dynamic"):
         kw["storages"] = tuple(args.storages.split(","))
+    if args.filter and args.which in ("paper", "dynamic"):
+        kw["filter_mode"] = args.filter
     if args.surfaces and args.which == "dynamic":
         kw["surfaces"] = tuple(tuple(float(v) for v in t.split(","))
                                for t in args.surfaces.split(";"))

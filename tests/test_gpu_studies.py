@@ -96,3 +96,20 @@ def test_paper_theta_table_trend_offset_and_drop_size(studies):
     for ga in low:
         v = [th[(r0, ga)]["surface"] for r0 in (30.0, 50.0, 65.0)]
         assert max(v) - min(v) <= max(7.0, 0.1 * float(np.mean(v))), (ga, v)
+
+
+def test_printed_angles_lie_between_two_readings_of_the_wall_filter(studies):
+    """The Appendix filter prints an outer sum over passes.  Read as one filter
+    pass per iterate (the oracle's and the library's reading) the drops wet
+    more than the paper reports; read as the mean of the iterates G^(1)..G^(N)
+    they wet less: at every G_A of Sec. III B the printed angle lies strictly
+    between the two (R0 = 50, 650x150, 40k steps)."""
+    gas = (0.0, 0.2, 0.5, 0.7, 0.9)
+    cases = [(50.0, ga) for ga in gas]
+    it = studies.paper_drops(cases, steps=40000, chunk=20000, filter_mode="iterate")
+    mn = studies.paper_drops(cases, steps=40000, chunk=20000, filter_mode="mean")
+    for ga, a, b in zip(gas, it["rows"], mn["rows"]):
+        lo, hi = a["theta_deg"]["surface"], b["theta_deg"]["surface"]
+        assert lo < studies.PAPER_THETA[ga] < hi, (ga, lo, studies.PAPER_THETA[ga], hi)
+    # the hydrodynamic boundary (phi_S = 0.01), printed as y_w = 8.5: 9.8 and 7.9
+    assert it["y_hydrodynamic"] > 8.5 > mn["y_hydrodynamic"]
