@@ -553,6 +553,10 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
+  // Every node has at most one periodic image column and one image row, and
+  // the images of a node pair are a pair again (even nx): the paired store of
+  // the ghost images applies.
+  const bool simple_images = a.nx >= 2 * GX && a.ny >= 2 * GY && (a.nx & 1) == 0;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
   const uint32_t key = step_key<S, MODE, FL>(a);
@@ -939,9 +943,26 @@ __device__ __forceinline__ bool march_segment_v2(const PopMaps* src, const CUten
                 out[Planes<Q>::template plane<i> * a.plane] = PR::lane(raw[i], 0);
               });
             }
-            const bool edge = (strip_edge && (xp < GX || xp + 1 >= a.nx - GX)) || yo < GY ||
-                              yo >= a.ny - GY;
-            if (edge) {
+            const bool xedge = strip_edge && (xp < GX || xp + 1 >= a.nx - GX);
+            const bool yedge = yo < GY || yo >= a.ny - GY;
+            if ((xedge || yedge) && pair_ok && simple_images) {
+              // Both nodes of the pair have the same images: at most one
+              // column shift (+-nx) and one row shift (+-ny), stored as pairs.
+              const int sx = !xedge ? 0 : (xp < GX ? a.nx : -a.nx);
+              const int64_t sy = !yedge ? 0 : (int64_t)(yo < GY ? a.ny : -a.ny) * a.pitch;
+              auto put = [&](int64_t d) {
+                static_for<0, Q>([&](auto ic) {
+                  constexpr int i = decltype(ic)::value;
+                  *reinterpret_cast<typename PR::Raw*>(out + d + Planes<Q>::template plane<i> * a.plane) =
+                      raw[i];
+                });
+              };
+              if (sx != 0) put(sx);
+              if (sy != 0) {
+                put(sy);
+                if (sx != 0) put(sy + sx);
+              }
+            } else if (xedge || yedge) {
   #pragma unroll 1
               for (int e = 0; e < 2; ++e) {
                 const int xn = xp + e;
