@@ -333,7 +333,7 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
     a sheared film.  Times `steps` steps run one lattice after another (one
     launch per lattice per step) against the same steps of all lattices in one
     batch (one fused launch per 32-lattice chunk per step, chunks on forked
-    streams, two-step CUDA graph, autotuned tiles)."""
+    streams, 16-step CUDA graphs, autotuned tiles)."""
     ws = W.batch_sweep(n=n, seed=2)
     nodes = sum(w.nx * w.ny for w in ws)
     sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
@@ -348,9 +348,9 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
     b = pkg.Batch()
     for sm in sims:
         b.add(sm)
-    tune = b.autotune(steps_per_trial=10)
+    tune = b.autotune(steps_per_trial=32)
     launches = b.launches_per_step()
-    b.step(4)
+    b.step(36)  # rebuild with the chosen tiling and capture both step graphs
     b.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()

@@ -262,9 +262,11 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
 
 /* A batch advances several contexts (its members) together: every time step is
  * one launch of one fused kernel per chunk of up to 32 members, whose CTAs march
- * a list of (member, strip, segment) tiles; the chunks run on streams forked
- * from the batch stream, and two consecutive steps are captured once in a CUDA
- * graph and replayed.  Members must share lattice and storage but may
+ * the chunk's (member, strip, segment) tiles, each launched as a programmatic
+ * dependent of the chunk's previous step; the chunks run on streams forked
+ * from the batch stream, and runs of 16 and of 2 consecutive steps are
+ * captured once in CUDA graphs and replayed (the chunk streams join at the end
+ * of each replay).  Members must share lattice and storage but may
  * differ in size and in every physical parameter.  Members stay owned by the
  * caller (destroy a member only after removing it), keep their own device
  * memory, and can still be read with lbm_moments and friends between batch
@@ -291,7 +293,7 @@ int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas);
 /* Advances every member by nsteps time steps; enqueued on the batch stream. */
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
 /* Times each candidate tiling (rows 4..64 x {one CTA per tile, one persistent
- * wave}) for steps_per_trial steps (plus 2 warm-up steps) on the members
+ * wave}) for steps_per_trial steps (plus 18 warm-up steps) on the members
  * themselves -- so they advance by those steps -- and keeps the fastest.
  * Outputs may be NULL.  Synchronises the stream. */
 int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile_rows,

@@ -822,6 +822,10 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
+// Steps per replay of the batch's long captured graph (even: the graph
+// returns the buffers to the parity it started from).
+constexpr int kLongSteps = 16;
+
 struct lbm_batch {
   lbm_allocator alloc{};
   bool user_alloc = false;
@@ -835,13 +839,10 @@ struct lbm_batch {
   bool dirty = true;
   void* d_members = nullptr;
   size_t cap_members = 0;
-  void* d_tiles = nullptr;
-  size_t cap_tiles = 0;
-  void* d_first = nullptr;
-  size_t cap_first = 0;
   int ntiles = 0, nctas = 0;
   int64_t phase = 0;
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec = nullptr;       // two steps
+  cudaGraphExec_t gexec_long = nullptr;  // kLongSteps steps
   cudaEvent_t order_ev = nullptr;  // orders member streams with the batch stream
   // Members are launched in chunks of up to kBatchChunk, each with its step
   // arguments as a kernel parameter.  With several chunks every chunk has its
@@ -850,7 +851,7 @@ struct lbm_batch {
   struct Chunk {
     std::vector<unsigned char> args;  // host copy of BatchArgs<T, S>
     int base = 0, count = 0;          // members [base, base + count)
-    int tile_off = 0, first_off = 0, nctas = 0;
+    int nctas = 0;
     bool plain = false;               // every member: exponential psi, no projection, SR
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -921,6 +922,10 @@ void drop_graph(lbm_batch* b) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
   }
+  if (b->gexec_long) {
+    cudaGraphExecDestroy(b->gexec_long);
+    b->gexec_long = nullptr;
+  }
 }
 
 void release_chunk(lbm_batch::Chunk& ch) {
@@ -955,10 +960,11 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
   }
   for (size_t k = nchunk; k < b->chunks.size(); ++k) release_chunk(b->chunks[k]);
   b->chunks.resize(nchunk);
-  // Tiles per chunk in row-band-major order (all strips of a segment before
-  // the next), member indices local to the chunk.
-  std::vector<std::vector<BatchTile>> ctiles(nchunk);
+  // Tiles per chunk, member by member; within a member segment by segment
+  // (all strips of a segment before the next).  The kernel derives each
+  // CTA's tile from its block index and these counts.
   size_t total = 0;
+  std::vector<int> chunk_tiles(nchunk, 0);
   for (int k = 0; k < nchunk; ++k) {
     lbm_batch::Chunk& ch = b->chunks[k];
     ch.base = k * kBatchChunk;
@@ -966,6 +972,7 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     ch.args.assign(sizeof(A), 0);
     A* pa = reinterpret_cast<A*>(ch.args.data());
     ch.plain = true;
+    int32_t t0 = 0;
     for (int i = 0; i < ch.count; ++i) {
       lbm_ctx* c = b->members[ch.base + i];
       ch.plain = ch.plain && c->p.psi_kind == LBM_PSI_EXP && !c->p.project &&
@@ -977,44 +984,25 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
       // remainder segment would pay its 2R halo rows and its pipeline fill
       // for a few rows only.
       const int L = std::max(1, std::min(b->tile_rows > 0 ? b->tile_rows : c->tile_rows, c->p.ny));
-      const int nseg = std::max(1, (c->p.ny + L / 2) / L);
-      for (int j = 0; j < nseg; ++j) {
-        const int y0 = (int)((int64_t)c->p.ny * j / nseg);
-        const int y1 = (int)((int64_t)c->p.ny * (j + 1) / nseg);
-        for (int x0 = 0; x0 < c->p.nx; x0 += W)
-          ctiles[k].push_back({i, x0, y0, y1 - y0, j & 1});
-      }
+      pa->nseg[i] = std::max(1, (c->p.ny + L / 2) / L);
+      pa->nstrip[i] = (c->p.nx + W - 1) / W;
+      pa->tile0[i] = t0;
+      t0 += pa->nseg[i] * pa->nstrip[i];
     }
-    total += ctiles[k].size();
+    for (int i = ch.count; i <= kBatchChunk; ++i) pa->tile0[i] = t0;
+    chunk_tiles[k] = t0;
+    total += (size_t)t0;
   }
-  std::vector<BatchTile> order;
-  std::vector<int32_t> first;
   b->nctas = 0;
   for (int k = 0; k < nchunk; ++k) {
     lbm_batch::Chunk& ch = b->chunks[k];
-    const std::vector<BatchTile>& tiles = ctiles[k];
-    ch.tile_off = (int)order.size();
-    ch.first_off = (int)first.size();
-    if (b->ctas <= 0) {
-      ch.nctas = (int)tiles.size();
-      order.insert(order.end(), tiles.begin(), tiles.end());
-      for (size_t t = 0; t <= tiles.size(); ++t) first.push_back((int32_t)t);
-    } else {
-      // Persistent CTAs (the batch's count shared out by tiles), tiles dealt
-      // round-robin: CTA j gets tiles j, j + G, ...
-      const int G = (int)std::max<size_t>(
-          1, std::min(tiles.size(), (size_t)std::llround((double)b->ctas * tiles.size() / total)));
-      ch.nctas = G;
-      int32_t local = 0;
-      for (int j = 0; j < G; ++j) {
-        first.push_back(local);
-        for (size_t t = j; t < tiles.size(); t += G) {
-          order.push_back(tiles[t]);
-          ++local;
-        }
-      }
-      first.push_back(local);
-    }
+    // Persistent CTAs: the batch's count shared out by tiles; CTA j of a
+    // chunk marches its tiles j, j + G, ...
+    ch.nctas = b->ctas <= 0
+                   ? chunk_tiles[k]
+                   : (int)std::max<int64_t>(
+                         1, std::min<int64_t>(chunk_tiles[k],
+                                              std::llround((double)b->ctas * chunk_tiles[k] / total)));
     b->nctas += ch.nctas;
     if (nchunk > 1 && !ch.stream) {
       BCK(b, cudaStreamCreateWithFlags(&ch.stream, cudaStreamNonBlocking));
@@ -1022,17 +1010,11 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
     }
   }
   if (nchunk > 1 && !b->fork_ev) BCK(b, cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
-  b->ntiles = (int)order.size();
+  b->ntiles = (int)total;
   batch_ctas_per_sm<Q, S>();  // sets the kernel's shared-memory attribute outside any capture
   int rc = bgrow(b, &b->d_members, &b->cap_members, sizeof(M) * std::max(1, n));
-  if (!rc) rc = bgrow(b, &b->d_tiles, &b->cap_tiles, sizeof(BatchTile) * std::max<size_t>(1, order.size()));
-  if (!rc) rc = bgrow(b, &b->d_first, &b->cap_first, sizeof(int32_t) * std::max<size_t>(1, first.size()));
   if (rc) return rc;
   BCK(b, cudaMemcpyAsync(b->d_members, hm.data(), sizeof(M) * n, cudaMemcpyHostToDevice, b->stream));
-  BCK(b, cudaMemcpyAsync(b->d_tiles, order.data(), sizeof(BatchTile) * order.size(),
-                         cudaMemcpyHostToDevice, b->stream));
-  BCK(b, cudaMemcpyAsync(b->d_first, first.data(), sizeof(int32_t) * first.size(),
-                         cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));  // host vectors go out of scope
   b->phase = 0;
   drop_graph(b);
@@ -1048,10 +1030,8 @@ template <int Q, typename S> cudaError_t batch_launch(lbm_batch* b, int parity) 
   for (const lbm_batch::Chunk& ch : b->chunks) {
     cudaError_t e = launch_batch<Q, S>(
         *reinterpret_cast<const BatchArgs<T, S>*>(ch.args.data()),
-        static_cast<const BatchMember<T, S>*>(b->d_members) + ch.base,
-        static_cast<const BatchTile*>(b->d_tiles) + ch.tile_off,
-        static_cast<const int32_t*>(b->d_first) + ch.first_off, ch.nctas, parity, b->ctas > 0,
-        ch.plain, multi ? ch.stream : b->stream);
+        static_cast<const BatchMember<T, S>*>(b->d_members) + ch.base, ch.nctas, parity,
+        b->ctas > 0, ch.plain, multi ? ch.stream : b->stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1195,25 +1175,38 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     return LBM_OK;
   };
   int64_t left = nsteps;
-  // Bring the phase to even, then replay a captured two-step graph.
+  // Bring the phase to even, then replay captured graphs of kLongSteps steps
+  // (the chunk streams join once per graph) and of two steps.
   if (b->phase & 1) {
     if ((rc = launch({1}))) return rc;
     b->phase += 1;
     left -= 1;
   }
-  if (left >= 2 && b->stream != nullptr && !b->gexec) {
+  auto capture = [&](std::initializer_list<int> parities, cudaGraphExec_t* out) -> int {
     cudaGraph_t graph = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    const int r = launch({0, 1});
+    const int r = launch(parities);
     cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
     if (r) {
       if (graph) cudaGraphDestroy(graph);
       return r;
     }
     BCK(b, ee);
-    cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     BCK(b, ei);
+    return LBM_OK;
+  };
+  if (left >= kLongSteps && b->stream != nullptr && !b->gexec_long) {
+    if ((rc = capture({0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1}, &b->gexec_long))) return rc;
+  }
+  while (left >= kLongSteps && b->gexec_long) {
+    BCK(b, cudaGraphLaunch(b->gexec_long, b->stream));
+    b->phase += kLongSteps;
+    left -= kLongSteps;
+  }
+  if (left >= 2 && b->stream != nullptr && !b->gexec) {
+    if ((rc = capture({0, 1}, &b->gexec))) return rc;
   }
   while (left >= 2) {
     if (b->gexec) {
@@ -1259,7 +1252,8 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile
       b->tile_rows = tr;
       b->ctas = ct;
       b->dirty = true;
-      if ((rc = lbm_batch_step(b, 2))) break;
+      // warm-up: rebuild, capture both graphs
+      if ((rc = lbm_batch_step(b, kLongSteps + 2))) break;
       cudaEventRecord(e0, b->stream);
       if ((rc = lbm_batch_step(b, steps_per_trial))) break;
       cudaEventRecord(e1, b->stream);
@@ -1298,8 +1292,6 @@ int lbm_batch_destroy(lbm_batch* b) {
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->order_ev) cudaEventDestroy(b->order_ev);
   bfree(b, b->d_members);
-  bfree(b, b->d_tiles);
-  bfree(b, b->d_first);
   delete b;
   return LBM_OK;
 }

@@ -40,15 +40,15 @@ cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
 // CTAs of the step kernel that fit on one SM (occupancy query).
 template <int Q, typename S> int step_ctas_per_sm();
 
-// One time step of up to kBatchChunk members of a batch (CTA b marches tiles
-// [first[b], first[b + 1])), and its residency per SM.  `plain`: every member
-// has the exponential psi, no projection and (16-bit storage) stochastic
-// rounding, so the kernel with those settings fixed runs.
+// One time step of up to kBatchChunk members of a batch: nctas CTAs, one per
+// tile of the chunk, or (persistent) each marching every nctas-th tile; and
+// the batch kernel's residency per SM.  `plain`: every member has the
+// exponential psi, no projection and (16-bit storage) stochastic rounding, so
+// the kernel with those settings fixed runs.
 template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
-                         const BatchMember<typename Codec<S>::T, S>* members,
-                         const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         bool persistent, bool plain, cudaStream_t stream);
+                         const BatchMember<typename Codec<S>::T, S>* members, int nctas,
+                         int parity, bool persistent, bool plain, cudaStream_t stream);
 template <int Q, typename S> int batch_ctas_per_sm();
 
 // Auxiliary kernels (aux.cu).

@@ -94,30 +94,35 @@ static cudaError_t prepare_batch_kernel() {
 template <int Q, typename S, int FL>
 static cudaError_t launch_batch_fl(const BatchArgs<typename Codec<S>::T, S>& args,
                                    const BatchMember<typename Codec<S>::T, S>* members,
-                                   const BatchTile* tiles, const int32_t* first, int nctas,
-                                   int parity, bool persistent, cudaStream_t stream) {
+                                   int nctas, int parity, bool persistent, cudaStream_t stream) {
   using Cfg = StepConfig<Q, S>;
   using Sh = ConfigShape<Q, S>;
   cudaError_t e = prepare_batch_kernel<Q, S, FL>();
   if (e != cudaSuccess) return e;
+  // A programmatic dependent launch, as for the single-lattice step.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(Sh::NT);
+  cfg.dynamicSmemBytes = Sh::SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (persistent)
-    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>
-        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
-  else
-    batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>
-        <<<nctas, Sh::NT, Sh::SMEM, stream>>>(args, members, tiles, first, parity);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>,
+                              args, members, parity);
+  return cudaLaunchKernelEx(&cfg, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>,
+                            args, members, parity);
 }
 
 template <int Q, typename S>
 cudaError_t launch_batch(const BatchArgs<typename Codec<S>::T, S>& args,
-                         const BatchMember<typename Codec<S>::T, S>* members,
-                         const BatchTile* tiles, const int32_t* first, int nctas, int parity,
-                         bool persistent, bool plain, cudaStream_t stream) {
-  return plain ? launch_batch_fl<Q, S, kFlExpPlain>(args, members, tiles, first, nctas, parity,
-                                                    persistent, stream)
-               : launch_batch_fl<Q, S, kFlRuntime>(args, members, tiles, first, nctas, parity,
-                                                   persistent, stream);
+                         const BatchMember<typename Codec<S>::T, S>* members, int nctas,
+                         int parity, bool persistent, bool plain, cudaStream_t stream) {
+  return plain ? launch_batch_fl<Q, S, kFlExpPlain>(args, members, nctas, parity, persistent, stream)
+               : launch_batch_fl<Q, S, kFlRuntime>(args, members, nctas, parity, persistent, stream);
 }
 
 // Residency per SM of the persistent batch kernel; also sets the shared-memory
@@ -144,6 +149,5 @@ template <int Q, typename S> int batch_ctas_per_sm() {
   template int lbm::step_ctas_per_sm<Q, S>();                                            \
   template cudaError_t lbm::launch_batch<Q, S>(                                          \
       const lbm::BatchArgs<lbm::Codec<S>::T, S>&,                                         \
-      const lbm::BatchMember<lbm::Codec<S>::T, S>*, const lbm::BatchTile*, const int32_t*, \
-      int, int, bool, bool, cudaStream_t);                                               \
+      const lbm::BatchMember<lbm::Codec<S>::T, S>*, int, int, bool, bool, cudaStream_t);    \
   template int lbm::batch_ctas_per_sm<Q, S>();

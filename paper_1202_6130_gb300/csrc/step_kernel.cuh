@@ -1073,50 +1073,60 @@ template <typename T, typename S> struct BatchMember {
 };
 
 // Step arguments of up to kBatchChunk members of a batch for either direction
-// (a[m][d] reads buffer d and writes buffer 1 - d), and the buffer holding
-// each member's state at parity 0.  Passed as a kernel parameter, so the
-// kernel reads them from constant memory: read-only, unlike a copy in shared
-// memory that every per-row barrier would force the compiler to reload.
+// (a[m][d] reads buffer d and writes buffer 1 - d), the buffer holding each
+// member's state at parity 0, and the chunk's tiles: member m owns tiles
+// [tile0[m], tile0[m + 1]), nseg[m] segments of nstrip[m] strips numbered
+// segment by segment (tile0[m] = the chunk's tile count past its last member).
+// Passed as a kernel parameter, so the kernel reads them from constant memory
+// with the CTA-uniform member index that it derives from its block index.
 constexpr int kBatchChunk = 32;
 template <typename T, typename S> struct BatchArgs {
   StepArgs<T, S> a[kBatchChunk][2];
   int32_t cur[kBatchChunk];
+  int32_t tile0[kBatchChunk + 1];
+  int32_t nstrip[kBatchChunk];
+  int32_t nseg[kBatchChunk];
 };
 
-// One segment of one member lattice (member: index within the launch's chunk);
-// rev != 0 marches it upwards (odd segments, as in step_kernel).
-struct BatchTile {
-  int32_t member, x0, y0, rows, rev;
-};
-
-// One time step of up to kBatchChunk lattices of a batch.  With PERSIST, CTA
-// b marches tiles [first[b], first[b + 1]) in order; otherwise CTA b marches
-// tile b (no loop state held across the march).  `parity` flips the
-// read/write buffers on alternate steps.  FL as for step_kernel (kFlExpPlain
-// when every member of the chunk has those settings).
+// One time step of up to kBatchChunk lattices of a batch.  Tile t is segment
+// t / nstrip (rows balanced over the member's height, odd segments marched
+// upwards as in step_kernel) and strip t % nstrip of its member.  With
+// PERSIST, CTA b marches tiles b, b + gridDim.x, ...; otherwise CTA b marches
+// tile b.  `parity` flips the read/write buffers on alternate steps.  FL as
+// for step_kernel (kFlExpPlain when every member of the chunk has those
+// settings).
 template <int Q, typename S, int W, int NS, int MINB, bool PERSIST, int FL>
 __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
     batch_step_kernel(const __grid_constant__ BatchArgs<typename Codec<S>::T, S> P,
                       const BatchMember<typename Codec<S>::T, S>* __restrict__ members,
-                      const BatchTile* __restrict__ tiles, const int32_t* __restrict__ first,
                       int32_t parity) {
   extern __shared__ unsigned char smem_raw[];
   const auto sm = StepSmem<Q, S, W, NS>::carve(smem_raw);
   const uint64_t policy = step_smem_init(sm);
   uint32_t g = 0;
+  // A programmatic dependent of the chunk's previous step (see step_kernel).
+  griddep_launch_dependents();
+  griddep_wait();
   auto march_tile = [&](int t) -> bool {
-    const BatchTile tile = tiles[t];
-    const int dir = (P.cur[tile.member] ^ parity) & 1;
-    const auto& a = P.a[tile.member][dir];
-    if (threadIdx.x == 0 && tile.x0 == 0 && tile.y0 == 0) advance_key<kModeStep>(a);
-    const auto* m = &members[tile.member];
-    return march_any<Q, S, W, NS, kModeStep, FL>(&m->map[dir], &m->flags, a, tile.x0, tile.y0,
-                                            tile.rows, tile.rev != 0, sm, g, policy);
+    int m = 0;
+#pragma unroll
+    for (int j = 1; j < kBatchChunk; ++j) m += t >= P.tile0[j] ? 1 : 0;
+    const int local = t - P.tile0[m];
+    const int seg = local / P.nstrip[m];
+    const int x0 = (local - seg * P.nstrip[m]) * W;
+    const int dir = (P.cur[m] ^ parity) & 1;
+    const auto& a = P.a[m][dir];
+    const int y0 = (int)((int64_t)a.ny * seg / P.nseg[m]);
+    const int y1 = (int)((int64_t)a.ny * (seg + 1) / P.nseg[m]);
+    if (threadIdx.x == 0 && local == 0) advance_key<kModeStep>(a);
+    const auto* mb = &members[m];
+    return march_any<Q, S, W, NS, kModeStep, FL>(&mb->map[dir], &mb->flags, a, x0, y0, y1 - y0,
+                                                (seg & 1) != 0, sm, g, policy);
   };
   if constexpr (PERSIST) {
-    const int t1 = first[blockIdx.x + 1];
+    const int nt = P.tile0[kBatchChunk];
 #pragma unroll 1
-    for (int t = first[blockIdx.x]; t < t1; ++t)
+    for (int t = blockIdx.x; t < nt; t += gridDim.x)
       if (!march_tile(t)) return;
   } else {
     march_tile((int)blockIdx.x);

@@ -251,7 +251,7 @@ class Batch:
 
     def __init__(self, stream=None, use_torch_allocator: bool = True, device=None):
         """``stream``: the stream batch steps run on; by default a new stream, so
-        that two steps can be captured in a CUDA graph.  Each step is ordered
+        that runs of steps can be captured in CUDA graphs.  Each step is ordered
         with the members' streams by the library (events both ways)."""
         import torch
         self.lib = L.load()
