@@ -825,6 +825,7 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
 // Steps per replay of the batch's long captured graph (even: the graph
 // returns the buffers to the parity it started from).
 constexpr int kLongSteps = 16;
+static_assert(kLongSteps % 2 == 0, "a replay must end on the parity it started from");
 
 struct lbm_batch {
   lbm_allocator alloc{};
@@ -1153,13 +1154,15 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   }
   // Steps with the given parities: fork the chunk streams from the batch
   // stream, launch each chunk's steps on its stream, join them back.
-  auto launch = [&](std::initializer_list<int> parities) -> int {
+  // Steps with parities parity0, parity0 ^ 1, ... (n of them).
+  auto launch = [&](int parity0, int n) -> int {
     const bool multi = b->chunks.size() > 1;
     if (multi) {
       BCK(b, cudaEventRecord(b->fork_ev, b->stream));
       for (const lbm_batch::Chunk& ch : b->chunks) BCK(b, cudaStreamWaitEvent(ch.stream, b->fork_ev, 0));
     }
-    for (int parity : parities) {
+    for (int j = 0; j < n; ++j) {
+      const int parity = parity0 ^ (j & 1);
       const int r = dispatch(b->Q, b->storage, [&]<int Q, typename S>() -> int {
         BCK(b, batch_launch<Q, S>(b, parity));
         return LBM_OK;
@@ -1178,14 +1181,14 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   // Bring the phase to even, then replay captured graphs of kLongSteps steps
   // (the chunk streams join once per graph) and of two steps.
   if (b->phase & 1) {
-    if ((rc = launch({1}))) return rc;
+    if ((rc = launch(1, 1))) return rc;
     b->phase += 1;
     left -= 1;
   }
-  auto capture = [&](std::initializer_list<int> parities, cudaGraphExec_t* out) -> int {
+  auto capture = [&](int n, cudaGraphExec_t* out) -> int {
     cudaGraph_t graph = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    const int r = launch(parities);
+    const int r = launch(0, n);
     cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
     if (r) {
       if (graph) cudaGraphDestroy(graph);
@@ -1198,7 +1201,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     return LBM_OK;
   };
   if (left >= kLongSteps && b->stream != nullptr && !b->gexec_long) {
-    if ((rc = capture({0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1}, &b->gexec_long))) return rc;
+    if ((rc = capture(kLongSteps, &b->gexec_long))) return rc;
   }
   while (left >= kLongSteps && b->gexec_long) {
     BCK(b, cudaGraphLaunch(b->gexec_long, b->stream));
@@ -1206,19 +1209,19 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     left -= kLongSteps;
   }
   if (left >= 2 && b->stream != nullptr && !b->gexec) {
-    if ((rc = capture({0, 1}, &b->gexec))) return rc;
+    if ((rc = capture(2, &b->gexec))) return rc;
   }
   while (left >= 2) {
     if (b->gexec) {
       BCK(b, cudaGraphLaunch(b->gexec, b->stream));
     } else {
-      if ((rc = launch({0, 1}))) return rc;
+      if ((rc = launch(0, 2))) return rc;
     }
     b->phase += 2;
     left -= 2;
   }
   if (left == 1) {
-    if ((rc = launch({0}))) return rc;
+    if ((rc = launch(0, 1))) return rc;
     b->phase += 1;
   }
   // Later work on a member's stream sees the batch's steps.

@@ -14,18 +14,29 @@ namespace lbm {
 // sized for, per (lattice, storage).  Shared memory per CTA is
 // NS * (Q box slots + flag slot) + the psi ring.
 // (Measured on GB300, 8192x4096: D2Q9 NS 4 / MINB 8 for FP32 and MINB 10 for
-// 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12; D2Q21 needs NS >= R + 2
-// = 5, and NS 5 with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3
-// by 21% and 5%.  16-bit D2Q21 runs 6 CTAs of 64 threads (node pairs) once
-// its plane groups arrive as boxes of depth 1, 3 and 7 (37 KB per CTA).)
+// 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12 (16-bit at MINB 12: 76
+// registers, 0.243 ms against 0.233); D2Q21 needs NS >= R + 2 = 5, and NS 5
+// with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3 by 21% and
+// 5%.  16-bit D2Q21 runs 6 CTAs of 64 threads (node pairs) once its plane
+// groups arrive as boxes of depth 1, 3 and 7 (37 KB per CTA).)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
   static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 5)) : 5;
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
                                        : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 6));
-  // The batch kernel carries its tile loop on top of the march: 16-bit D2Q9
-  // targets 8 CTAs per SM there, so that it does not spill.
+  // The persistent batch kernel carries its tile loop on top of the march:
+  // 16-bit D2Q9 targets 8 CTAs per SM there, so that it does not spill.
   static constexpr int BATCH_MINB = (Q == 9 && sizeof(S) == 2) ? 8 : MINB;
+  // One CTA per tile, the compile-time-flag kernel (kFlExpPlain): D2Q9 FP32
+  // and 16-bit batches run 12 CTAs per SM (76-80 registers, no spills; the
+  // 256-lattice sweep 6% faster than at 10 for FP16S, 1.4% than at 8 for
+  // FP32): short tiles of many small lattices need more CTAs in flight than
+  // the single lattice's long strips.  The run-time-flag kernel keeps MINB (it
+  // would spill at 12).
+  static constexpr int BATCH_MINB_PLAIN = (Q == 9 && sizeof(S) != 8) ? 12 : MINB;
+  template <int FL> static constexpr int batch_minb_tile() {
+    return FL == kFlExpPlain ? BATCH_MINB_PLAIN : MINB;
+  }
 };
 
 template <int Q, typename S>

@@ -82,7 +82,7 @@ static cudaError_t prepare_batch_kernel() {
   using Sh = ConfigShape<Q, S>;
   static cudaError_t once = [] {
     cudaError_t e = cudaFuncSetAttribute(
-        batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>,
+        batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::template batch_minb_tile<FL>(), false, FL>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>,
@@ -113,7 +113,7 @@ static cudaError_t launch_batch_fl(const BatchArgs<typename Codec<S>::T, S>& arg
   if (persistent)
     return cudaLaunchKernelEx(&cfg, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::BATCH_MINB, true, FL>,
                               args, members, parity);
-  return cudaLaunchKernelEx(&cfg, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::MINB, false, FL>,
+  return cudaLaunchKernelEx(&cfg, batch_step_kernel<Q, S, Cfg::W, Cfg::NS, Cfg::template batch_minb_tile<FL>(), false, FL>,
                             args, members, parity);
 }
 

@@ -271,6 +271,8 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
   const uint32_t g0 = g;
   const bool wall_on = a.wall.active != 0;
   const bool strip_edge = x0 < GX || x0 + W > a.nx - GX;
+  // Every node has at most one periodic image column and one image row.
+  const bool simple_images = a.nx >= 2 * GX && a.ny >= 2 * GY;
   const uint32_t tx_bytes = Sh::TX_POP + (wall_on ? Sh::TX_FLAGS : 0u) + a.extra_tx;
   constexpr int kIss = kIssuer<Sh::NT>;
 
@@ -453,9 +455,24 @@ __device__ __forceinline__ bool march_segment(const PopMaps* src, const CUtensor
           });
           // Periodic images exist only for nodes within GX of a side or GY of
           // the top or bottom; the strip test is per CTA, the row test per row.
-          const bool edge = (strip_edge && (x < GX || x >= a.nx - GX)) || yo < GY ||
-                            yo >= a.ny - GY;
-          if (edge) {
+          const bool xedge = strip_edge && (x < GX || x >= a.nx - GX);
+          const bool yedge = yo < GY || yo >= a.ny - GY;
+          if ((xedge || yedge) && simple_images) {
+            // at most one image column (+-nx) and one image row (+-ny)
+            const int sx = !xedge ? 0 : (x < GX ? a.nx : -a.nx);
+            const int64_t sy = !yedge ? 0 : (int64_t)(yo < GY ? a.ny : -a.ny) * a.pitch;
+            auto put = [&](int64_t d) {
+              static_for<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                out[d + Planes<Q>::template plane<i> * a.plane] = e[i];
+              });
+            };
+            if (sx != 0) put(sx);
+            if (sy != 0) {
+              put(sy);
+              if (sx != 0) put(sy + sx);
+            }
+          } else if (xedge || yedge) {
             int xa = x;
             while (xa - a.nx >= -GX) xa -= a.nx;
             int ya = yo;
