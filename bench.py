@@ -332,7 +332,7 @@ def measure_batch(pkg, torch, W, storage: str = "fp16s", steps: int = 200, n: in
     64x32 .. 1024x512 (seed 2), each with its own tau, G, G_R, G_A and a drop or
     a sheared film.  Times `steps` steps run one lattice after another (one
     launch per lattice per step) against the same steps of all lattices in one
-    batch (one fused launch per 32-lattice chunk per step, chunks on forked
+    batch (one fused launch per 64-lattice chunk per step, chunks on forked
     streams, 16-step CUDA graphs, autotuned tiles)."""
     ws = W.batch_sweep(n=n, seed=2)
     nodes = sum(w.nx * w.ny for w in ws)

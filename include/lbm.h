@@ -261,7 +261,8 @@ int lbm_wall_core_tail(int32_t nx, int32_t ny, const double* dist, const double*
 /* ---- batches: many lattices advanced by shared launches --------------------- */
 
 /* A batch advances several contexts (its members) together: every time step is
- * one launch of one fused kernel per chunk of up to 32 members, whose CTAs march
+ * one launch of one fused kernel per chunk of up to 64 members (32 with FP64
+ * storage), whose CTAs march
  * the chunk's (member, strip, segment) tiles, each launched as a programmatic
  * dependent of the chunk's previous step; the chunks run on streams forked
  * from the batch stream, and runs of 16 and of 2 consecutive steps are
@@ -285,7 +286,8 @@ int lbm_batch_add(lbm_batch* b, lbm_ctx* c);
 int lbm_batch_remove(lbm_batch* b, lbm_ctx* c);
 int lbm_batch_size(const lbm_batch* b, int32_t* n);
 /* Kernel launches per batch time step: the number of member chunks (members
- * divided by 32, rounded up; 0 for an empty batch). */
+ * divided by 64, or by 32 with FP64 storage, rounded up; 0 for an empty
+ * batch). */
 int lbm_batch_launches_per_step(const lbm_batch* b, int32_t* n);
 /* Tile shape: tile_rows rows per segment (0: each member's own choice) and
  * ctas persistent CTAs that deal the tiles round-robin (0: one CTA per tile). */

@@ -845,7 +845,7 @@ struct lbm_batch {
   cudaGraphExec_t gexec = nullptr;       // two steps
   cudaGraphExec_t gexec_long = nullptr;  // kLongSteps steps
   cudaEvent_t order_ev = nullptr;  // orders member streams with the batch stream
-  // Members are launched in chunks of up to kBatchChunk, each with its step
+  // Members are launched in chunks of up to BatchArgs::kChunk, each with its step
   // arguments as a kernel parameter.  With several chunks every chunk has its
   // own stream, forked from and joined back to the batch stream around each
   // sequence of steps (a member depends only on its own previous step).
@@ -945,7 +945,8 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
   using A = BatchArgs<T, S>;
   constexpr int W = StepConfig<Q, S>::W;
   const int n = (int)b->members.size();
-  const int nchunk = (n + kBatchChunk - 1) / kBatchChunk;
+  constexpr int kChunk = A::kChunk;
+  const int nchunk = (n + kChunk - 1) / kChunk;
   std::vector<M> hm(n);
   b->versions.assign(n, 0);
   b->cur0.assign(n, 0);
@@ -968,8 +969,8 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
   std::vector<int> chunk_tiles(nchunk, 0);
   for (int k = 0; k < nchunk; ++k) {
     lbm_batch::Chunk& ch = b->chunks[k];
-    ch.base = k * kBatchChunk;
-    ch.count = std::min(kBatchChunk, n - ch.base);
+    ch.base = k * kChunk;
+    ch.count = std::min(kChunk, n - ch.base);
     ch.args.assign(sizeof(A), 0);
     A* pa = reinterpret_cast<A*>(ch.args.data());
     ch.plain = true;
@@ -990,7 +991,7 @@ template <int Q, typename S> int batch_build(lbm_batch* b) {
       pa->tile0[i] = t0;
       t0 += pa->nseg[i] * pa->nstrip[i];
     }
-    for (int i = ch.count; i <= kBatchChunk; ++i) pa->tile0[i] = t0;
+    for (int i = ch.count; i <= kChunk; ++i) pa->tile0[i] = t0;
     chunk_tiles[k] = t0;
     total += (size_t)t0;
   }
@@ -1119,7 +1120,8 @@ int lbm_batch_size(const lbm_batch* b, int32_t* n) {
 
 int lbm_batch_launches_per_step(const lbm_batch* b, int32_t* n) {
   if (!b || !n) return bfail(nullptr, LBM_EINVAL, "null argument");
-  *n = (int32_t)((b->members.size() + kBatchChunk - 1) / kBatchChunk);
+  const int chunk = b->storage == LBM_FP64 ? batch_chunk<double>() : batch_chunk<float>();
+  *n = (int32_t)((b->members.size() + chunk - 1) / chunk);
   return LBM_OK;
 }
 

@@ -1089,23 +1089,28 @@ template <typename T, typename S> struct BatchMember {
   CUtensorMap flags;
 };
 
-// Step arguments of up to kBatchChunk members of a batch for either direction
+// Step arguments of up to kChunk members of a batch for either direction
 // (a[m][d] reads buffer d and writes buffer 1 - d), the buffer holding each
 // member's state at parity 0, and the chunk's tiles: member m owns tiles
 // [tile0[m], tile0[m + 1]), nseg[m] segments of nstrip[m] strips numbered
 // segment by segment (tile0[m] = the chunk's tile count past its last member).
 // Passed as a kernel parameter, so the kernel reads them from constant memory
 // with the CTA-uniform member index that it derives from its block index.
-constexpr int kBatchChunk = 32;
+// kChunk: 64 members with FP32 arithmetic, 32 with FP64 (the larger FP64
+// arguments), so that the block stays below the 32,764-byte parameter limit.
+template <typename T> constexpr int batch_chunk() { return sizeof(T) == 8 ? 32 : 64; }
 template <typename T, typename S> struct BatchArgs {
-  StepArgs<T, S> a[kBatchChunk][2];
-  int32_t cur[kBatchChunk];
-  int32_t tile0[kBatchChunk + 1];
-  int32_t nstrip[kBatchChunk];
-  int32_t nseg[kBatchChunk];
+  static constexpr int kChunk = batch_chunk<T>();
+  StepArgs<T, S> a[kChunk][2];
+  int32_t cur[kChunk];
+  int32_t tile0[kChunk + 1];
+  int32_t nstrip[kChunk];
+  int32_t nseg[kChunk];
 };
+static_assert(sizeof(BatchArgs<float, float>) <= 32764 && sizeof(BatchArgs<double, double>) <= 32764,
+              "batch arguments fit the kernel parameter space");
 
-// One time step of up to kBatchChunk lattices of a batch.  Tile t is segment
+// One time step of up to kChunk lattices of a batch.  Tile t is segment
 // t / nstrip (rows balanced over the member's height, odd segments marched
 // upwards as in step_kernel) and strip t % nstrip of its member.  With
 // PERSIST, CTA b marches tiles b, b + gridDim.x, ...; otherwise CTA b marches
@@ -1127,7 +1132,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
   auto march_tile = [&](int t) -> bool {
     int m = 0;
 #pragma unroll
-    for (int j = 1; j < kBatchChunk; ++j) m += t >= P.tile0[j] ? 1 : 0;
+    for (int j = 1; j < P.kChunk; ++j) m += t >= P.tile0[j] ? 1 : 0;
     const int local = t - P.tile0[m];
     const int seg = local / P.nstrip[m];
     const int x0 = (local - seg * P.nstrip[m]) * W;
@@ -1141,7 +1146,7 @@ __global__ void __launch_bounds__(StepShape<Q, S, W, NS>::NT, MINB)
                                                 (seg & 1) != 0, sm, g, policy);
   };
   if constexpr (PERSIST) {
-    const int nt = P.tile0[kBatchChunk];
+    const int nt = P.tile0[P.kChunk];
 #pragma unroll 1
     for (int t = blockIdx.x; t < nt; t += gridDim.x)
       if (!march_tile(t)) return;

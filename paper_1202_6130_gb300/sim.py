@@ -246,7 +246,8 @@ class Simulation:
 
 class Batch:
     """Several Simulations of one (lattice, storage) kind advanced together: one
-    fused launch per chunk of up to 32 members per time step (lbm_batch_* of
+    fused launch per chunk of up to 64 members (32 with FP64 storage) per time
+    step (lbm_batch_* of
     include/lbm.h)."""
 
     def __init__(self, stream=None, use_torch_allocator: bool = True, device=None):
@@ -281,7 +282,8 @@ class Batch:
         self.stream.synchronize()
 
     def launches_per_step(self) -> int:
-        """Kernel launches per batch time step (one per chunk of up to 32 members)."""
+        """Kernel launches per batch time step (one per chunk of up to 64 members,
+        32 with FP64 storage)."""
         n = ctypes.c_int32()
         self._chk(self.lib.lbm_batch_launches_per_step(self.h, ctypes.byref(n)))
         return n.value

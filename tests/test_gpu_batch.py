@@ -149,12 +149,12 @@ def test_member_reinitialised_between_batch_steps(pkg):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16s"])
 def test_many_members_span_several_launch_chunks(pkg, storage):
-    """70 lattices: three launch chunks of at most 32 members, each chunk on its
+    """140 lattices: three launch chunks of at most 64 members, each chunk on its
     own stream forked from and joined to the batch stream inside the two-step
     graph.  Every member still equals its solo run bit for bit, across an odd
     step count."""
     ws = [W.droplet_on_wall(nx=24 + 4 * (k % 7), ny=16 + 2 * (k % 5), R=5.0, seed=100 + k,
-                            noise_amp=1e-5, tau=0.7 + 0.01 * k, G_A=0.001 * k) for k in range(70)]
+                            noise_amp=1e-5, tau=0.7 + 0.005 * k, G_A=0.0005 * k) for k in range(140)]
     want = [_alone(pkg, w, storage, 5) for w in ws]
     sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
     b = pkg.Batch()
