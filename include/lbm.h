@@ -296,10 +296,19 @@ int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas);
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
 /* Times each candidate tiling (rows 4..64 x {one CTA per tile, one persistent
  * wave}) for steps_per_trial steps (plus 18 warm-up steps) on the members
- * themselves -- so they advance by those steps -- and keeps the fastest.
+ * themselves -- so they advance by those steps -- keeps the fastest, and
+ * records it for the batch's size class (see lbm_batch_use_tuned).
  * Outputs may be NULL.  Synchronises the stream. */
 int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile_rows,
                        int32_t* best_ctas, double* best_ms_per_step);
+/* The tiling lbm_batch_autotune last chose for a batch of the same lattice,
+ * storage and size class (floor(log2) of the total node count and of the
+ * member count), kept process-wide: when there is one, it becomes b's tiling
+ * and *found = 1; otherwise b is unchanged and *found = 0.  Advances nothing,
+ * so a batch whose members must not take extra steps (a serving loop) can use
+ * a tiling tuned earlier on a similar batch.  Errors: LBM_EINVAL (found
+ * NULL). */
+int lbm_batch_use_tuned(lbm_batch* b, int32_t* found);
 int lbm_batch_destroy(lbm_batch* b); /* NULL ok; members are untouched */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
@@ -313,11 +322,12 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * host framework that forbids cudaMalloc after start-up.  The paper has no
  * counterpart; this is a service of the library.
  *
- * It calls no cudaMalloc / cudaFree and no allocating library routine.  Its
- * partial sums live in one fixed 192 KiB array in device memory, which every
- * GPU that loads the library holds until the process exits; that bounds n to
- * at most 2^28 elements (4096 blocks of 65536), and larger n returns LBM_EINVAL
- * with the limit in lbm_last_error(NULL).  The first call on a device looks up
+ * It runs the kernels and block partition of lbm_totals (1024 blocks, merged
+ * in block order), so the same arrays give the same bits, and it calls no
+ * cudaMalloc / cudaFree and no allocating library routine: its partial sums
+ * live in one fixed 48 KiB array in device memory, which every GPU that loads
+ * the library holds until the process exits.  n has no limit beyond int64_t.
+ * The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) once, with the device
  * current; with CUDA's default lazy module loading that first call is also
  * when the array and these kernels are loaded onto the device, which takes
@@ -331,7 +341,7 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * synchronising.  Every call on a device shares the one array, so calls whose
  * kernels overlap on the GPU (different streams, no ordering between them)
  * race and give wrong sums; calls on one stream are safe.  Errors: LBM_EINVAL
- * (out NULL, n < 0 or above the limit), LBM_ECUDA (launch failure). */
+ * (out NULL or n < 0), LBM_ECUDA (launch failure). */
 int lbm_reduce3_noalloc(const double* d_a, const double* d_b, const double* d_c, int64_t n,
                         double* d_out3, void* cuda_stream);
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "lbm_batch_size": (c_int, [c_void_p, POINTER(c_int32)]),
     "lbm_batch_launches_per_step": (c_int, [c_void_p, POINTER(c_int32)]),
     "lbm_batch_set_tiling": (c_int, [c_void_p, c_int32, c_int32]),
+    "lbm_batch_use_tuned": (c_int, [c_void_p, POINTER(c_int32)]),
     "lbm_batch_step": (c_int, [c_void_p, c_int64]),
     "lbm_batch_autotune": (c_int, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
                                    POINTER(c_double)]),

@@ -11,6 +11,9 @@
 #include <new>
 #include <string>
 #include <initializer_list>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -407,7 +410,7 @@ int lbm_create(const lbm_params* p, const lbm_allocator* a, void* cuda_stream, l
   rc = dispatch(p->lattice, p->storage, [&]<int Q, typename S>() { return setup_layout<Q, S>(c); });
   if (rc == LBM_OK) {
     c->d_status = static_cast<uint32_t*>(dalloc(c, 256));
-    c->nparts = 1024;
+    c->nparts = kReduceParts;
     c->d_partials = static_cast<double*>(dalloc(c, sizeof(double) * 6 * c->nparts));
     c->d_out3 = static_cast<double*>(dalloc(c, 256));
     if (!c->d_status || !c->d_partials || !c->d_out3)
@@ -1135,6 +1138,58 @@ int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_rows, int32_t ctas) {
   return LBM_OK;
 }
 
+namespace {
+// Tilings chosen by lbm_batch_autotune, per (lattice, storage, size class):
+// the size class is floor(log2(nodes)) of the batch's total node count and
+// floor(log2(members)).  Process-wide, shared by every batch.
+struct TuneKey {
+  int q, storage, nodes_log2, members_log2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(q, storage, nodes_log2, members_log2) <
+           std::tie(o.q, o.storage, o.nodes_log2, o.members_log2);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+int floor_log2(int64_t v) {
+  int r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+TuneKey tune_key(const lbm_batch* b) {
+  int64_t nodes = 0;
+  for (const lbm_ctx* c : b->members) nodes += (int64_t)c->p.nx * c->p.ny;
+  return TuneKey{b->Q, b->storage, floor_log2(nodes), floor_log2((int64_t)b->members.size())};
+}
+}  // namespace
+
+int lbm_batch_use_tuned(lbm_batch* b, int32_t* found) {
+  int rc = batch_guard(b);
+  if (rc) return rc;
+  if (!found) return bfail(b, LBM_EINVAL, "null argument");
+  *found = 0;
+  if (b->members.empty()) return LBM_OK;
+  std::pair<int, int> t;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(tune_key(b));
+    if (it == g_tuned.end()) return LBM_OK;
+    t = it->second;
+  }
+  if (t.first != b->tile_rows || t.second != b->ctas) {
+    b->tile_rows = t.first;
+    b->ctas = t.second;
+    b->dirty = true;
+  }
+  *found = 1;
+  return LBM_OK;
+}
+
 int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   int rc = batch_guard(b);
   if (rc) return rc;
@@ -1282,6 +1337,10 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, int32_t* best_tile
   b->tile_rows = bt;
   b->ctas = bc;
   b->dirty = true;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[tune_key(b)] = {bt, bc};
+  }
   if (best_tile_rows) *best_tile_rows = bt;
   if (best_ctas) *best_ctas = bc;
   if (best_ms_per_step) *best_ms_per_step = best;

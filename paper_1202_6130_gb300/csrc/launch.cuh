@@ -79,8 +79,12 @@ cudaError_t launch_wall_prepare(const double* phi, const double* psr, const doub
                                 int ny, T* phie, T* sx, T* sy, T* uwx, T* uwy, uint32_t* flags,
                                 int nchunk_pad, cudaStream_t st);
 
-// Sum of rho_s candidates: sum_i f_i over all nodes of an FP64 [Q][N] array
-// (fsum) or of an [N] array (rho).  Deterministic two-pass Neumaier reduction.
+// Compensated (Neumaier) FP64 sums of up to three [N] arrays (NULL sums to
+// 0) into out[3]: nparts blocks each reduce a grid-stride share into
+// partials[6 * nparts], then one thread merges them in block order
+// (deterministic).  lbm_totals and lbm_reduce3_noalloc both use kReduceParts
+// blocks.
+constexpr int kReduceParts = 1024;
 cudaError_t launch_reduce3(const double* a, const double* b, const double* c, int64_t n,
                            double* partials, int nparts, double* out, cudaStream_t st);
 cudaError_t launch_colsum(const double* f, int q, int64_t n, double* out_n, cudaStream_t st);

@@ -127,6 +127,9 @@ class Server:
         self.keep_fields = keep_fields
         self.workload = workload
         self.batch = Batch()
+        # tiling: (tile_rows, ctas), or None for the tiling an earlier autotune
+        # chose for the batch's current size class, when there is one
+        self.tiling = tiling
         if tiling is not None:
             self.batch.set_tiling(*tiling)
         self.side = torch.cuda.Stream()
@@ -215,6 +218,8 @@ class Server:
                 self._collect()
                 return bool(self.queue)
         q = min(self.quantum, min(v[3] for v in self.active.values()))
+        if self.tiling is None:
+            self.batch.use_tuned()
         self.batch.step(q)
         self._stage()
         self._collect()

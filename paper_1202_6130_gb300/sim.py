@@ -294,6 +294,13 @@ class Batch:
     def step(self, n: int = 1):
         self._chk(self.lib.lbm_batch_step(self.h, int(n)))
 
+    def use_tuned(self) -> bool:
+        """Adopt the tiling an earlier autotune chose for a batch of the same
+        lattice, storage and size class (advances nothing); False if none."""
+        found = ctypes.c_int32()
+        self._chk(self.lib.lbm_batch_use_tuned(self.h, ctypes.byref(found)))
+        return bool(found.value)
+
     def autotune(self, steps_per_trial: int = 20):
         tr, ct, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
         self._chk(self.lib.lbm_batch_autotune(self.h, int(steps_per_trial), ctypes.byref(tr),

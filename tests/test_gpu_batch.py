@@ -98,6 +98,39 @@ def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
     b.close()
 
 
+def test_tuned_tiling_is_kept_per_size_class(pkg):
+    """autotune records its choice for the batch's (lattice, storage, size
+    class); another batch of that class adopts it without stepping, one of
+    another class (or storage) finds none; bits do not depend on the tiling."""
+    ws = [W.droplet_on_wall(nx=40 + 8 * k, ny=24 + 4 * k, R=6.0, seed=300 + k, noise_amp=1e-5)
+          for k in range(4)]
+    tuned = pkg.Batch()
+    for w in ws:
+        tuned.add(pkg.Simulation.from_workload(w, storage="bf16s"))
+    best = tuned.autotune(steps_per_trial=4)
+    tuned.close()
+    same = [pkg.Simulation.from_workload(w, storage="bf16s") for w in ws]
+    b = pkg.Batch()
+    for s in same:
+        b.add(s)
+    assert b.use_tuned()
+    assert all(s.steps_done() == 0 for s in same)
+    b.step(5)
+    for s, w in zip(same, ws):
+        np.testing.assert_array_equal(s.populations(), _alone(pkg, w, "bf16s", 5))
+    b.close()
+    big = pkg.Batch()
+    big.add(pkg.Simulation.from_workload(W.droplet_on_wall(nx=256, ny=128, R=20.0), storage="bf16s"))
+    assert not big.use_tuned()
+    big.close()
+    other = pkg.Batch()
+    for w in ws:
+        other.add(pkg.Simulation.from_workload(w, storage="fp16s"))
+    assert not other.use_tuned()
+    other.close()
+    assert best["tile_rows"] > 0
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16s", "bf16s"])
 def test_d2q21_paper_fluid_batch_equals_members_alone_bitwise(pkg, storage):
     """D2Q21 (one node per thread in FP64 and FP32, node pairs in 16-bit
