@@ -51,7 +51,7 @@ cudaError_t launch_step(const PopMaps& src, const CUtensorMap& flags,
 // CTAs of the step kernel that fit on one SM (occupancy query).
 template <int Q, typename S> int step_ctas_per_sm();
 
-// One time step of up to kBatchChunk members of a batch: nctas CTAs, one per
+// One time step of up to BatchArgs::kChunk members of a batch: nctas CTAs, one per
 // tile of the chunk, or (persistent) each marching every nctas-th tile; and
 // the batch kernel's residency per SM.  `plain`: every member has the
 // exponential psi, no projection and (16-bit storage) stochastic rounding, so

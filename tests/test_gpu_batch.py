@@ -3,8 +3,8 @@
 Each member's node arithmetic is the same as when it runs alone, so a member's
 populations after n batch steps must equal, bit for bit, those after n steps on
 its own -- for every tiling, with persistent CTAs, across odd step counts (the
-two-step graph plus a single launch) and when members are stepped on their
-own or removed between batch steps."""
+16- and 2-step graphs plus single launches) and when members are stepped on
+their own or removed between batch steps."""
 import numpy as np
 import pytest
 
@@ -98,6 +98,30 @@ def test_batch_rejects_mixed_kinds_and_autotunes(pkg):
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["fp32", "bf16s"])
+def test_long_graph_replays_equal_members_alone_bitwise(pkg, storage):
+    """37 steps from parity 0 replay the 16-step graph twice, the 2-step graph
+    twice and one single launch; 16 more from parity 1 start with a single
+    launch and then replay the 16-step graph from the other parity's side.
+    Drops of uneven sizes and a body-force-driven channel equal their solo
+    runs bit for bit."""
+    ws = [W.droplet_on_wall(nx=48 + 16 * k, ny=24 + 8 * k, R=6.0 + k, seed=500 + k,
+                            noise_amp=1e-5, tau=0.8 + 0.1 * k) for k in range(3)]
+    ws.append(W.poiseuille_channel(nx=32, ny=40, force=2e-6))
+    sims = [pkg.Simulation.from_workload(w, storage=storage) for w in ws]
+    b = pkg.Batch()
+    for s_ in sims:
+        b.add(s_)
+    b.step(37)
+    for s_, w in zip(sims, ws):
+        assert s_.steps_done() == 37
+        np.testing.assert_array_equal(s_.populations(), _alone(pkg, w, storage, 37))
+    b.step(16)
+    for s_, w in zip(sims, ws):
+        np.testing.assert_array_equal(s_.populations(), _alone(pkg, w, storage, 53))
+    b.close()
+
+
 def test_tuned_tiling_is_kept_per_size_class(pkg):
     """autotune records its choice for the batch's (lattice, storage, size
     class); another batch of that class adopts it without stepping, one of
@@ -183,8 +207,8 @@ def test_member_reinitialised_between_batch_steps(pkg):
 @pytest.mark.parametrize("storage", ["fp32", "fp16s"])
 def test_many_members_span_several_launch_chunks(pkg, storage):
     """140 lattices: three launch chunks of at most 64 members, each chunk on its
-    own stream forked from and joined to the batch stream inside the two-step
-    graph.  Every member still equals its solo run bit for bit, across an odd
+    own stream forked from and joined to the batch stream inside each graph
+    replay.  Every member still equals its solo run bit for bit, across an odd
     step count."""
     ws = [W.droplet_on_wall(nx=24 + 4 * (k % 7), ny=16 + 2 * (k % 5), R=5.0, seed=100 + k,
                             noise_amp=1e-5, tau=0.7 + 0.005 * k, G_A=0.0005 * k) for k in range(140)]
