@@ -180,6 +180,9 @@ def test_fp64_ragged_and_multi_tile_match_oracle(pkg, case):
 PAIRED_CASES = [dict(nx=67, ny=35, tile_rows=5), dict(nx=1, ny=16, tile_rows=4),
                 dict(nx=3, ny=1, tile_rows=0), dict(nx=129, ny=7, tile_rows=3, uwall=True,
                                                     body=(1e-5, 0.0)),
+                # even widths at the edge of the paired ghost-image store: nx = 2 GX of
+                # 16-bit storage with ny = 2 GY, and one column and row above it
+                dict(nx=16, ny=4, tile_rows=2), dict(nx=18, ny=5, tile_rows=0, uwall=True),
                 # D2Q21 (R = 3): odd widths, several tiles, a moving wall, the Eq. EOS fluid
                 dict(nx=67, ny=35, lattice=21, tile_rows=5), dict(nx=3, ny=9, lattice=21, tile_rows=2),
                 dict(nx=131, ny=13, lattice=21, tile_rows=4, uwall=True, body=(1e-5, 0.0)),
@@ -192,8 +195,8 @@ PAIRED_CASES = [dict(nx=67, ny=35, tile_rows=5), dict(nx=1, ny=16, tile_rows=4),
 def test_paired_path_ragged_sizes_match_oracle(pkg, case, storage, tol):
     """The two-nodes-per-thread path (D2Q9 in FP32 and 16-bit storage, D2Q21 in
     16-bit storage; D2Q21 FP32 runs one node per thread) on odd widths (a lone
-    last column), a one-column and a one-row lattice, many tiles, after 40
-    steps.  FP32: 1e-5 in rho and u.  16-bit storage: rho within 8e-3 (FP16S,
+    last column), a one-column and a one-row lattice, even widths where every
+    pair's ghost images are stored as pairs, many tiles, after 40 steps.  FP32: 1e-5 in rho and u.  16-bit storage: rho within 8e-3 (FP16S,
     about three times the largest error over these cases) and eight times that
     for BF16S (three fewer significant bits); u within three times the rho
     bound, relative to its maximum."""
