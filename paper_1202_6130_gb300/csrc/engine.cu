@@ -200,14 +200,14 @@ template <int Q, typename S> int make_tmap(lbm_ctx* c, int which) {
 // active tiles in a compact band of rows and balance the SMs dynamically; with
 // adjacent segments marching in opposite directions the 2R halo rows they
 // share are pulled at about the same time and the second pull hits in L2.
-// FP32 is fastest at 4-6 rows (0.367-0.370 ms against 0.385 ms at 12), 16-bit
-// storage near 24, FP64 near 64.  Small
+// FP32 is fastest at 4-5 rows (0.3640 ms against 0.3668 at 6, 0.3722 at 8 and
+// 0.3775 at 3), 16-bit storage near 24, FP64 near 64.  Small
 // lattices get shorter segments so that the grid still covers at least two
 // waves of resident CTAs.
 int choose_tile_rows(int nx, int ny, int W, int esize, int R, int ctas_per_sm, int num_sms) {
   const int gx = (nx + W - 1) / W;
   const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * num_sms;
-  int L = esize == 2 ? 24 : (esize == 4 ? 6 : 64);
+  int L = esize == 2 ? 24 : (esize == 4 ? 4 : 64);
   if (R > 1) L = std::max(L, 16 * R);
   while (L > 4 && (int64_t)gx * ((ny + L - 1) / L) < 2 * slots) L /= 2;
   return std::max(1, std::min(L, ny));
