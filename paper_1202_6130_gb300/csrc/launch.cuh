@@ -17,11 +17,14 @@ namespace lbm {
 // 16-bit storage beat NS 5 / MINB 6 and MINB 8 or 12 (16-bit at MINB 12: 76
 // registers, 0.243 ms against 0.233); D2Q21 needs NS >= R + 2 = 5, and NS 5
 // with 3 CTAs per SM (FP32) or 5 (16-bit) beat NS 6 with 2 or 3 by 21% and
-// 5%.  16-bit D2Q21 runs 6 CTAs of 64 threads (node pairs) once its plane
-// groups arrive as boxes of depth 1, 3 and 7 (37 KB per CTA).)
+// 5%.  16-bit D2Q21 runs CTAs of 64 threads (node pairs), its plane groups
+// arriving as boxes of depth 1, 3 and 7: NS 6 (43 KB, 5 CTAs per SM: two rows
+// in flight besides the four the collision re-reads) beat NS 5 (6 CTAs) by 1.1%
+// and NS 7 (4 CTAs) by 8%.)
 template <int Q, typename S> struct StepConfig {
   static constexpr int W = 128;
-  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 5)) : 5;
+  static constexpr int NS = (Q == 9) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 4 ? 4 : 5))
+                                     : (sizeof(S) == 2 ? 6 : 5);
   static constexpr int MINB = (Q == 9) ? (sizeof(S) == 8 ? 2 : (sizeof(S) == 4 ? 8 : 10))
                                        : (sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 6));
   // The persistent batch kernel carries its tile loop on top of the march:
