@@ -464,6 +464,42 @@ def test_paper_eos_flat_interface_density_ratio_d2q21():
     assert abs(rl / rv - ratio) / ratio < tol
 
 
+def _eos_drop(R, n=48, steps=1500):
+    """Free drop of the paper fluid (D2Q21, Eq. EOS, G = -1/theta, projection
+    on) of initial radius R on an n x n periodic lattice: its radius from the
+    liquid area and p_in - p_out with p = p_EOS(rho)."""
+    p = O.paper_profile(O.D2Q21, tau=1.0)
+    rho = W.droplet_density(n, n, [(n / 2.0, n / 2.0)], [R], 1.0, 0.1, 2.0)
+    z = np.zeros_like(rho)
+    r, _, _ = O.macroscopic(p, None, O.run(p, None, O.initial_populations(p, rho, z, z), steps))
+    frac = np.clip((r - r.min()) / (r.max() - r.min()), 0.0, 1.0)
+    R_eq = math.sqrt(frac.sum() / math.pi)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    d = np.hypot(x - n / 2.0, y - n / 2.0)
+    pr = O.p_eos(p, r)
+    return R_eq, float(pr[d < R_eq - 4].mean() - pr[d > R_eq + 6].mean())
+
+
+def test_paper_eos_surface_tension_from_laplace_law_d2q21():
+    """Paper profile: the pressure jump across free drops (radii 7.5-14) is
+    linear in 1/R (Laplace's law in 2-D, dp = gamma / R) with a negligible
+    intercept, and the slope gamma is the printed surface tension of the
+    Eq. EOS fluid, 0.09, within 10% (the oracle gives 0.084).  This pins the
+    normalisation of the fluid-fluid force in magnitude (G = -1/theta with the
+    paper's psi): with G = -1 the fluid would not be the printed one."""
+    pv = _golden.paper_values()
+    pts = [_eos_drop(R) for R in (8.0, 11.0, 14.0)]
+    inv_r = np.array([1.0 / a for a, _ in pts])
+    dp = np.array([b for _, b in pts])
+    slope, icept = np.polyfit(inv_r, dp, 1)
+    fit = slope * inv_r + icept
+    r2 = 1.0 - np.sum((dp - fit) ** 2) / np.sum((dp - dp.mean()) ** 2)
+    gamma, tol = pv["surface_tension"]
+    assert r2 > 0.999, (r2, pts)
+    assert abs(icept) < 0.05 * dp.min(), (icept, pts)
+    assert abs(slope - gamma) < tol * gamma, (slope, pts)
+
+
 # --------------------------------------------------------------------------
 # Wall functions (Appendix)
 # --------------------------------------------------------------------------
